@@ -1,0 +1,19 @@
+"""CPU FP64 oracle for the ChASE hot path of arXiv 2006.08498.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+baseline leg of bench.py may import, call, link or execute anything in this
+package.  The product path (paper_2006_08498_gb300) never imports it and
+shares no code with it: the synthetic generator, the random streams and every
+step of the solver are written here independently of the CUDA kernels.
+
+Parity pins (tests/test_oracle_*.py) tie each function to something other
+than itself: closed forms, the paper's printed tables, brute force on tiny
+inputs, and library routines used as test-time cross-checks.
+"""
+from ._lib import build  # noqa: F401
+from .chase import (  # noqa: F401
+    STREAM_EXCHANGE, STREAM_LANCZOS, STREAM_START, STREAM_THETA, STREAM_XI,
+    bse_tables, build_h, chase, chebyshev_filter, cholesky, cholqr,
+    convergence_rate, default_model, degrees, eigh, filter_interval,
+    lanczos_bounds, lock_count, normalize_phase, qr, random_block,
+    rayleigh_ritz, residuals, splitmix64, tridiag_eig, uniform)
