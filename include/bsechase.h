@@ -1,0 +1,180 @@
+/*
+ * bsechase: ChASE (Chebyshev-accelerated subspace iteration) for the lowest
+ * eigenpairs of a dense complex Hermitian Bethe-Salpeter (exciton)
+ * Hamiltonian, on one GB300 GPU (sm_103a).
+ *
+ * The problem is the one of arXiv 2006.08498: the eigenproblem of the BSE
+ * Hamiltonian of Eq. (1) (Sec. 2), for the lowest part of the spectrum with
+ * eigenvectors (Sec. 2, the optical response needs the eigenvectors), with
+ * the solver's search-space parameters nev and nex (Sec. 3, and the nex
+ * study of the Supplement).  The solver's phases are those of the
+ * Supplement's ChASE timing breakdown: Lanczos, Filter, QR, Rayleigh-Ritz,
+ * Resid.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major: element (i, j) at p[i + j*ld], ld >= rows.
+ *  - Complex numbers are interleaved (re, im) doubles (C99 double complex,
+ *    torch.complex128).  A row-major Hermitian H passed as-is is conj(H):
+ *    same eigenvalues, conjugated eigenvectors.
+ *  - "d_" pointers are CUDA device pointers on the context's device; "h_"
+ *    pointers and plain double* outputs are host memory.
+ *  - The caller owns every buffer it passes; the library owns its workspace
+ *    (allocated in the context, grown on demand, freed by destroy) and never
+ *    frees caller memory.
+ *  - All device work is issued on the context's stream.  Entry points
+ *    return after their results are complete (host outputs written).
+ *  - Every call returns a status (bse_status); no exception crosses the
+ *    ABI.  bsechase_last_error() describes the last failure of a context.
+ */
+#ifndef BSECHASE_H
+#define BSECHASE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsechase_ctx bsechase_ctx;
+
+typedef enum {
+    BSE_OK = 0,
+    BSE_EINVAL = -1,     /* invalid argument (size, pointer, parameter)       */
+    BSE_ENOMEM = -2,     /* device workspace could not be allocated           */
+    BSE_ENOCONV = -3,    /* max_iter reached; converged pairs are returned and
+                            the residual of every other pair is +inf          */
+    BSE_ENONFINITE = -4, /* NaN/Inf met (in H or in a reduction), or a
+                            Cholesky factorisation failed                     */
+    BSE_ETIMEOUT = -5,   /* a bounded wait expired                            */
+    BSE_ECUDA = -6,      /* a CUDA runtime call failed                        */
+    BSE_EBUSY = -7       /* the request is still pending                      */
+} bse_status;
+
+typedef enum {
+    CHASE_FP64 = 0,         /* every phase in FP64                            */
+    CHASE_MIXED_FP32 = 1    /* filter products in complex FP32, closing FP64
+                               sweeps; QR, Rayleigh-Ritz, residuals in FP64   */
+} chase_precision;
+
+/* Parameters of the synthetic Eq. (1) Hamiltonian (energies in eV).
+ * NULL selects the defaults {2.0, 0.3, 0.5, 0.01, 1.0, 8}. */
+typedef struct {
+    double band_gap;    /* E_c(k=0,c=0) - E_v(k=0,v=0) without jitter         */
+    double w0;          /* strength of the screened direct term W             */
+    double x0;          /* strength of the exchange term 2 vbar               */
+    double jitter;      /* amplitude of the seeded conduction-band jitter     */
+    double dispersion;  /* scale of the cosine band dispersion                */
+    int rank_x;         /* rank of the exchange term (0..64)                  */
+} bse_model;
+
+/* Solver options; NULL selects the defaults. */
+typedef struct {
+    int deg_init;        /* first-iteration filter degree (default 20)       */
+    int max_iter;        /* iteration limit (default 50)                      */
+    int lanczos_steps;   /* steps per Lanczos run (default 25, <= 64)         */
+    int lanczos_vecs;    /* independent Lanczos runs (default 4, <= 8)        */
+    uint64_t seed;       /* seed of the Lanczos and start vectors (default 0) */
+    const void *d_V0;    /* optional warm start: N x n_v0 device block        */
+    int64_t ldv0;
+    int n_v0;            /* 0 = none; at most nev + nex columns are used      */
+} chase_opts;
+
+/* Per-solve statistics (times in milliseconds, CUDA events on the stream). */
+typedef struct {
+    int iters;              /* subspace iterations                            */
+    int locked;             /* pairs converged                                */
+    int64_t matvecs;        /* H*vector products: filter + RR + Lanczos       */
+    int64_t filter_matvecs; /* filter products only                          */
+    double ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid, ms_total;
+    double filter_tflops;   /* 8 N^2 filter_matvecs / filter time             */
+    double norm_est;        /* ||H|| estimate (Lanczos)                       */
+    double alpha, beta, lower; /* final damped interval and filter lower point */
+    int64_t kernel_launches;   /* CUDA kernels this solve launched            */
+    int64_t filter_launches;   /* filter matrix-product launches              */
+} chase_stats;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = a stream owned by the context). */
+int bsechase_create(bsechase_ctx **ctx, int device, void *cuda_stream);
+/* Free the context's workspace and stream (if owned).  NULL is ignored. */
+void bsechase_destroy(bsechase_ctx *ctx);
+/* Static description of a status code. */
+const char *bsechase_strerror(int status);
+/* Description of the last failure in `ctx` (empty string if none). */
+const char *bsechase_last_error(const bsechase_ctx *ctx);
+
+/* Dimension N = Nk * Nv * Nc of the BSE Hamiltonian (Sec. 2: the pair index
+ * runs over valence bands, conduction bands and k-points); -1 if invalid. */
+int64_t bse_dim(int Nk, int Nv, int Nc);
+
+/* Fill d_H (N x N complex128, column-major, leading dimension ldh >= N)
+ * with the seeded synthetic BSE Hamiltonian of Eq. (1):
+ *   H_IJ = dE_I delta_IJ + 2 sum_r a_r(I) conj(a_r(J))
+ *          - w0 [v=v', c=c'] e^{i(theta_I - theta_J)} / (d(k,k')^2 + 1/2),
+ * I = (k Nv + v) Nc + c, dE = E_c(k) - E_v(k) from cosine bands with jitter,
+ * d the distance on a periodic ring of Nk k-points, a_r, theta and the
+ * jitter drawn from SplitMix64 keyed by `seed`.  H is Hermitian bit for bit.
+ * Errors: BSE_EINVAL (sizes <= 0, N > 2^31, ldh < N, rank_x outside 0..64,
+ * NULL d_H), BSE_ECUDA. */
+int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
+                          const bse_model *model, void *d_H, int64_t ldh);
+
+/* Lowest nev eigenpairs of the Hermitian d_H (N x N complex128,
+ * column-major, ldh >= N) by ChASE (Sec. 3; Supplement, ChASE breakdown).
+ * Search space m = nev + nex (1 <= nev, 0 <= nex, m <= min(N, 512)).
+ * Converged means ||H v - lambda v||_2 / ||H||_est <= tol, ||H||_est from
+ * the Lanczos estimate; deg_max (>= 2) caps the per-vector filter degree.
+ * Outputs: h_evals[nev] ascending; d_evecs (N x nev complex128, ld = ldz >=
+ * N) orthonormal, each column's largest-modulus entry (smallest index on
+ * ties) real and positive; h_resid[nev]; stats (nullable).
+ * d_H is read only.  Errors: BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV (outputs
+ * filled, unconverged residuals +inf), BSE_ENONFINITE, BSE_ECUDA. */
+int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int nev, int nex,
+                double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
+                void *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
+
+/* As chase_solve with every matrix in HOST memory: h_H (N x N) is copied to
+ * a context-owned device buffer and the eigenvectors are copied back into
+ * h_evecs (N x nev, ld = ldz).  Host buffers should be pinned for full
+ * transfer speed.  Same errors as chase_solve. */
+int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh, int nev,
+                     int nex, double tol, int deg_max, int precision, const chase_opts *opts,
+                     double *h_evals, void *h_evecs, int64_t ldz, double *h_resid,
+                     chase_stats *stats);
+
+/* ---- single phases, on caller device buffers (the steps chase_solve runs) */
+
+/* Lanczos spectral estimate (Supplement, "Lanczos" item): `runs` Lanczos
+ * runs of `steps` steps from SplitMix64 start vectors (seed, stream 4).
+ * out[4] (host) = {beta (upper bound of lambda_N), mu_1 (estimate of
+ * lambda_1), mu_m (estimate of lambda_m), ||H|| estimate}. */
+int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int m,
+                  int steps, int runs, uint64_t seed, double *out);
+
+/* Chebyshev filter (Sec. 3; Supplement, "Filter" item): column j of d_V
+ * (N x m, ldv) is replaced by p_{d_j}(H) v_j, p_d(x) = T_d((x-c)/e) /
+ * T_d((lower-c)/e), via the scaled three-term recurrence.  h_deg[m] (host)
+ * must be ascending, each >= 1.  Returns the number of H*vector products
+ * in *matvecs (nullable). */
+int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, void *d_V,
+                 int64_t ldv, int m, const int *h_deg, double lower, double c, double e,
+                 int64_t *matvecs);
+
+/* QR phase (Supplement, "QR" item): d_V (N x m) becomes an orthonormal
+ * basis of span(d_V) projected off span(d_L) (d_L: N x k orthonormal, may
+ * be NULL with k = 0): two projections, column scaling, shifted Cholesky QR
+ * and two Cholesky QR passes each after a projection. */
+int chase_qr(bsechase_ctx *ctx, const void *d_L, int64_t ldl, int k, void *d_V, int64_t ldv,
+             int64_t N, int m);
+
+/* Rayleigh-Ritz (Supplement, "RR" item) for orthonormal d_Q (N x m):
+ * h_theta[m] ascending Ritz values; d_V = Q Y and d_HV = H Q Y (N x m,
+ * ld = N); h_resid[m] = ||HV_j - theta_j V_j|| / norm (nullable). */
+int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
+                        const void *d_Q, int64_t ldq, int m, double *h_theta, void *d_V,
+                        void *d_HV, double norm, double *h_resid);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSECHASE_H */

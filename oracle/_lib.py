@@ -63,6 +63,9 @@ def lib():
         L.or_bse_build.argtypes = [u64, i32, i32, i32, ctypes.POINTER(Model),
                                    P, i64]
         L.or_bse_build.restype = None
+        L.or_bse_elements.argtypes = [u64, i32, i32, i32, ctypes.POINTER(Model),
+                                      i64, P, P, P]
+        L.or_bse_elements.restype = None
         L.or_tridiag_eig.argtypes = [i32, P, P, P]
         L.or_tridiag_eig.restype = i32
         L.or_heev.argtypes = [i32, P, i64, P, P, i64, i32]

@@ -65,6 +65,16 @@ def build_h(seed, Nk, Nv, Nc, model=None):
     return H
 
 
+def bse_elements(seed, Nk, Nv, Nc, I, J, model=None):
+    """H[I[t], J[t]] of the synthetic Hamiltonian without forming H."""
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.zeros(len(I), dtype=np.complex128)
+    _lib.lib().or_bse_elements(seed, Nk, Nv, Nc, _model(model), len(I), ptr(I), ptr(J),
+                               ptr(out))
+    return out
+
+
 def bse_tables(seed, Nk, Nv, Nc, model=None):
     """(dE[N], a[N, R], theta[N]) of the synthetic model."""
     N = Nk * Nv * Nc

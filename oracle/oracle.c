@@ -379,3 +379,23 @@ int or_cholesky(int n, zc *G, int64_t ld)
         for (int i = j + 1; i < n; i++) G[i + (int64_t)j * ld] = 0.0;
     return 0;
 }
+
+/* Selected elements H[I[t], J[t]] (t < n) of the synthetic Hamiltonian,
+ * without forming H (for spot checks at sizes where H is large). */
+void or_bse_elements(uint64_t seed, int Nk, int Nv, int Nc, const or_model *md,
+                     int64_t n, const int64_t *Iv, const int64_t *Jv, zc *out)
+{
+    const int64_t N = (int64_t)Nk * Nv * Nc;
+    double *dE = malloc(sizeof(double) * N);
+    double *theta = malloc(sizeof(double) * N);
+    zc *a = malloc(sizeof(zc) * N * (md->rank_x > 0 ? md->rank_x : 1));
+    or_bse_tables(seed, Nk, Nv, Nc, md, dE, a, theta);
+    for (int64_t t = 0; t < n; t++) {
+        int64_t i = Iv[t], j = Jv[t];
+        out[t] = (i >= j) ? bse_lower_element(i, j, Nk, Nv, Nc, md, dE, a, theta)
+                          : conj(bse_lower_element(j, i, Nk, Nv, Nc, md, dE, a, theta));
+    }
+    free(dE);
+    free(theta);
+    free(a);
+}

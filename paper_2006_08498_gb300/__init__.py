@@ -1,0 +1,302 @@
+"""ChASE for dense complex Hermitian BSE Hamiltonians on one GB300 GPU.
+
+Thin ctypes binding of the C ABI in include/bsechase.h (libbsechase.so, built
+in-tree by paper_2006_08498_gb300.build).  Every step of the solver runs in
+the library's CUDA kernels; this module only marshals arguments.  PyTorch
+supplies device memory and the stream.
+
+Column-major matrices are represented as torch tensors with strides
+(1, ld): ``colmajor_empty(rows, cols)`` allocates one, ``t.T.contiguous().T``
+converts any tensor.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libbsechase.so")
+
+BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV = 0, -1, -2, -3
+BSE_ENONFINITE, BSE_ETIMEOUT, BSE_ECUDA, BSE_EBUSY = -4, -5, -6, -7
+CHASE_FP64, CHASE_MIXED_FP32 = 0, 1
+
+# Every symbol include/bsechase.h declares.
+ABI_SYMBOLS = (
+    "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
+    "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
+    "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz",
+)
+
+
+class BseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_strerror(status), status, msg))
+        self.status = status
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("band_gap", ctypes.c_double), ("w0", ctypes.c_double),
+                ("x0", ctypes.c_double), ("jitter", ctypes.c_double),
+                ("dispersion", ctypes.c_double), ("rank_x", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("deg_init", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("lanczos_steps", ctypes.c_int), ("lanczos_vecs", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("d_V0", ctypes.c_void_p),
+                ("ldv0", ctypes.c_int64), ("n_v0", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("locked", ctypes.c_int),
+                ("matvecs", ctypes.c_int64), ("filter_matvecs", ctypes.c_int64),
+                ("ms_lanczos", ctypes.c_double), ("ms_filter", ctypes.c_double),
+                ("ms_qr", ctypes.c_double), ("ms_rr", ctypes.c_double),
+                ("ms_resid", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("filter_tflops", ctypes.c_double), ("norm_est", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("lower", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("filter_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+DEFAULT_MODEL = dict(band_gap=2.0, w0=0.3, x0=0.5, jitter=0.01, dispersion=1.0, rank_x=8)
+
+_lib = None
+
+
+def library_path():
+    return _LIBPATH
+
+
+def load():
+    """Load libbsechase.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIBPATH):
+        raise RuntimeError("libbsechase.so is not built; run "
+                           "`python -m paper_2006_08498_gb300.build` (nvcc, sm_103a)")
+    L = ctypes.CDLL(_LIBPATH)
+    P, i64, i32, dbl, u64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                             ctypes.c_double, ctypes.c_uint64)
+    DP = ctypes.POINTER(ctypes.c_double)
+    L.bsechase_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32, P]
+    L.bsechase_create.restype = i32
+    L.bsechase_destroy.argtypes = [P]
+    L.bsechase_destroy.restype = None
+    L.bsechase_strerror.argtypes = [i32]
+    L.bsechase_strerror.restype = ctypes.c_char_p
+    L.bsechase_last_error.argtypes = [P]
+    L.bsechase_last_error.restype = ctypes.c_char_p
+    L.bse_dim.argtypes = [i32, i32, i32]
+    L.bse_dim.restype = i64
+    L.bse_build_hamiltonian.argtypes = [P, u64, i32, i32, i32, ctypes.POINTER(Model), P, i64]
+    L.bse_build_hamiltonian.restype = i32
+    L.chase_solve.argtypes = [P, P, i64, i64, i32, i32, dbl, i32, i32, ctypes.POINTER(Opts),
+                              DP, P, i64, DP, ctypes.POINTER(Stats)]
+    L.chase_solve.restype = i32
+    L.chase_solve_host.argtypes = L.chase_solve.argtypes
+    L.chase_solve_host.restype = i32
+    L.chase_lanczos.argtypes = [P, P, i64, i64, i32, i32, i32, u64, DP]
+    L.chase_lanczos.restype = i32
+    L.chase_filter.argtypes = [P, P, i64, i64, P, i64, i32, ctypes.POINTER(ctypes.c_int),
+                               dbl, dbl, dbl, ctypes.POINTER(ctypes.c_int64)]
+    L.chase_filter.restype = i32
+    L.chase_qr.argtypes = [P, P, i64, i32, P, i64, i64, i32]
+    L.chase_qr.restype = i32
+    L.chase_rayleigh_ritz.argtypes = [P, P, i64, i64, P, i64, i32, DP, P, P, dbl, DP]
+    L.chase_rayleigh_ritz.restype = i32
+    _lib = L
+    return L
+
+
+def _strerror(status):
+    try:
+        return load().bsechase_strerror(status).decode()
+    except Exception:
+        return "status"
+
+
+def bse_dim(Nk, Nv, Nc):
+    return int(load().bse_dim(Nk, Nv, Nc))
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ld(t):
+    """Leading dimension of a column-major (strides (1, ld)) tensor/array."""
+    if hasattr(t, "stride") and callable(t.stride):
+        s = t.stride()
+        if s[0] != 1:
+            raise ValueError("matrix must be column-major (stride (1, ld))")
+        return max(s[1], t.shape[0]) if t.dim() == 2 else t.shape[0]
+    if not t.flags["F_CONTIGUOUS"]:
+        raise ValueError("array must be Fortran-ordered")
+    return t.shape[0]
+
+
+def colmajor_empty(rows, cols, device="cuda", dtype=None):
+    """Uninitialised column-major (rows x cols) torch tensor."""
+    import torch
+    dtype = torch.complex128 if dtype is None else dtype
+    return torch.empty((cols, rows), dtype=dtype, device=device).T
+
+
+class Context:
+    """A solver context on one device; work runs on torch's current stream
+    unless `stream` (a torch.cuda.Stream) is given."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self._torch = torch
+        L = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = L.bsechase_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream))
+        if rc != BSE_OK:
+            raise BseError(rc, "bsechase_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bsechase_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, allow=(BSE_OK,)):
+        if rc not in allow:
+            raise BseError(rc, load().bsechase_last_error(self._h).decode())
+        return rc
+
+    # ------------------------------------------------------------ generator
+    def build_hamiltonian(self, seed, Nk, Nv, Nc, model=None, out=None):
+        """Seeded synthetic Eq. (1) Hamiltonian as a column-major N x N
+        complex128 device tensor."""
+        N = bse_dim(Nk, Nv, Nc)
+        if N < 1:
+            raise ValueError("bad (Nk, Nv, Nc)")
+        if out is None:
+            out = colmajor_empty(N, N, device="cuda:%d" % self.device)
+        md = dict(DEFAULT_MODEL)
+        if model:
+            md.update(model)
+        m = Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
+                  int(md["rank_x"]))
+        rc = load().bse_build_hamiltonian(self._h, seed, Nk, Nv, Nc, ctypes.byref(m),
+                                          ctypes.c_void_p(out.data_ptr()), _ld(out))
+        self._check(rc)
+        return out
+
+    # -------------------------------------------------------------- solve
+    @staticmethod
+    def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0):
+        o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0)
+        if V0 is not None:
+            o.d_V0 = ctypes.c_void_p(V0.data_ptr())
+            o.ldv0 = _ld(V0)
+            o.n_v0 = V0.shape[1]
+        return o
+
+    def solve(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64, deg_init=20,
+              max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0, V0=None,
+              evecs=None, allow_noconv=False):
+        """Lowest nev eigenpairs of the device Hermitian H (column-major).
+        Returns (evals ndarray, evecs tensor N x nev, resid ndarray, stats)."""
+        N = H.shape[0]
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        if evecs is None:
+            evecs = colmajor_empty(N, nev, device=H.device)
+        st = Stats()
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0)
+        rc = load().chase_solve(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), nev, nex,
+                                tol, deg_max, precision, ctypes.byref(o), _dp(evals),
+                                ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
+                                ctypes.byref(st))
+        self._check(rc, (BSE_OK, BSE_ENOCONV) if allow_noconv else (BSE_OK,))
+        d = st.as_dict()
+        d["status"] = rc
+        return evals, evecs, resid, d
+
+    def solve_host(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
+                   deg_init=20, max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0,
+                   evecs=None):
+        """As solve(), with H and the eigenvectors in host memory (Fortran-
+        ordered complex128 numpy arrays, ideally pinned)."""
+        N = H.shape[0]
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        if evecs is None:
+            evecs = np.zeros((N, nev), dtype=np.complex128, order="F")
+        st = Stats()
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None)
+        hp = H.data_ptr() if hasattr(H, "data_ptr") else H.ctypes.data
+        ep = evecs.data_ptr() if hasattr(evecs, "data_ptr") else evecs.ctypes.data
+        rc = load().chase_solve_host(self._h, ctypes.c_void_p(hp), N, _ld(H), nev, nex, tol,
+                                     deg_max, precision, ctypes.byref(o), _dp(evals),
+                                     ctypes.c_void_p(ep), _ld(evecs), _dp(resid),
+                                     ctypes.byref(st))
+        self._check(rc)
+        d = st.as_dict()
+        d["status"] = rc
+        return evals, evecs, resid, d
+
+    # ------------------------------------------------------------- phases
+    def lanczos(self, H, m, steps=25, runs=4, seed=0):
+        out = np.zeros(4)
+        rc = load().chase_lanczos(self._h, ctypes.c_void_p(H.data_ptr()), H.shape[0], _ld(H),
+                                  m, steps, runs, seed, _dp(out))
+        self._check(rc)
+        return dict(beta=out[0], mu_1=out[1], mu_m=out[2], norm_est=out[3])
+
+    def filter(self, H, V, degrees, lower, c, e):
+        """In-place Chebyshev filter of the columns of V (ld must equal N)."""
+        deg = np.ascontiguousarray(degrees, dtype=np.int32)
+        mv = ctypes.c_int64(0)
+        rc = load().chase_filter(self._h, ctypes.c_void_p(H.data_ptr()), H.shape[0], _ld(H),
+                                 ctypes.c_void_p(V.data_ptr()), _ld(V), V.shape[1],
+                                 deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), lower, c, e,
+                                 ctypes.byref(mv))
+        self._check(rc)
+        return mv.value
+
+    def qr(self, V, L=None):
+        N, m = V.shape
+        k = 0 if L is None else L.shape[1]
+        rc = load().chase_qr(self._h, ctypes.c_void_p(L.data_ptr() if k else 0),
+                             _ld(L) if k else N, k, ctypes.c_void_p(V.data_ptr()), _ld(V), N, m)
+        self._check(rc)
+        return V
+
+    def rayleigh_ritz(self, H, Q, norm=1.0):
+        N, m = Q.shape
+        theta = np.zeros(m)
+        resid = np.zeros(m)
+        V = colmajor_empty(N, m, device=Q.device)
+        HV = colmajor_empty(N, m, device=Q.device)
+        rc = load().chase_rayleigh_ritz(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H),
+                                        ctypes.c_void_p(Q.data_ptr()), _ld(Q), m, _dp(theta),
+                                        ctypes.c_void_p(V.data_ptr()),
+                                        ctypes.c_void_p(HV.data_ptr()), norm, _dp(resid))
+        self._check(rc)
+        return theta, V, HV, resid

@@ -1,0 +1,675 @@
+// Host driver and C ABI of the ChASE solver (include/bsechase.h).
+//
+// The iteration follows the phases of the Supplement's ChASE breakdown
+// (Lanczos once, then Filter -> QR -> Rayleigh-Ritz -> Resid/lock until
+// nev pairs are locked).  Every phase runs in the kernels of gen.cu,
+// zgemm.cu, vec.cu and small.cu on the context's stream; the host only
+// sequences launches and reads back, once per iteration, the scalars and
+// the per-vector degrees that size the next filter's launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bsechase.h"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kMaxM = 512;
+constexpr double kU = 0x1.0p-53;
+constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct bsechase_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    ChaseScalars *sc = nullptr;      // device
+    ChaseScalars *hsc = nullptr;     // pinned host mirror
+    // workspace
+    DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
+    int64_t wsN = 0;
+    int wsM = 0;
+    cudaEvent_t ev[8];
+    bool ev_ok = false;
+};
+
+namespace {
+
+int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail = "") {
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, detail);
+    c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return fail(ctx, BSE_ECUDA, "CUDA error: %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+int ensure(bsechase_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes) return BSE_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (bytes == 0) return BSE_OK;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, BSE_ENOMEM, "cannot allocate %s of device workspace",
+                    std::to_string(bytes).c_str());
+    }
+    b.bytes = bytes;
+    return BSE_OK;
+}
+
+// Small-array layout inside small_d (doubles) and ints.
+struct Small {
+    double *theta, *resid, *norms, *lz_alpha, *lz_beta, *lam, *res;
+    int *deg, *perm, *order;
+};
+
+Small small_layout(bsechase_ctx *ctx, int m) {
+    Small s;
+    double *d = (double *)ctx->small_d.p;
+    s.theta = d;
+    s.resid = d + kMaxM;
+    s.norms = d + 2 * kMaxM;
+    s.lz_alpha = d + 3 * kMaxM;          // 64 x 8
+    s.lz_beta = d + 3 * kMaxM + 512;     // (64 + 1) x 8: row 0 = zeros
+    s.lam = d + 3 * kMaxM + 1088;
+    s.res = d + 4 * kMaxM + 1088;
+    int *ip = (int *)ctx->ints.p;
+    s.deg = ip;
+    s.perm = ip + kMaxM;
+    s.order = ip + 2 * kMaxM;
+    (void)m;
+    return s;
+}
+
+int ensure_workspace(bsechase_ctx *ctx, int64_t N, int m) {
+    int rc;
+    const size_t blk = (size_t)N * m * sizeof(z_t);
+    if ((rc = ensure(ctx, ctx->V, blk))) return rc;
+    if ((rc = ensure(ctx, ctx->B1, blk))) return rc;
+    if ((rc = ensure(ctx, ctx->B2, blk))) return rc;
+    if ((rc = ensure(ctx, ctx->B3, blk))) return rc;
+    const size_t sq = (size_t)kMaxM * kMaxM * sizeof(z_t);
+    if ((rc = ensure(ctx, ctx->G, sq))) return rc;
+    if ((rc = ensure(ctx, ctx->R, sq))) return rc;
+    if ((rc = ensure(ctx, ctx->Ri, sq))) return rc;
+    if ((rc = ensure(ctx, ctx->Yr, sq))) return rc;
+    if ((rc = ensure(ctx, ctx->heev, heev_work_bytes(kMaxM)))) return rc;
+    if ((rc = ensure(ctx, ctx->small_d, (size_t)(6 * kMaxM + 2048) * sizeof(double)))) return rc;
+    if ((rc = ensure(ctx, ctx->ints, (size_t)4 * kMaxM * sizeof(int)))) return rc;
+    const size_t cn = (size_t)kCnWork * sizeof(z_t);
+    const size_t vp = (size_t)vec_partial_blocks(N) * kMaxM * 2 * sizeof(double);
+    if ((rc = ensure(ctx, ctx->part, std::max(cn, vp)))) return rc;
+    if ((rc = ensure(ctx, ctx->lz, (size_t)N * 8 * 3 * sizeof(z_t)))) return rc;
+    ctx->wsN = N;
+    ctx->wsM = m;
+    return BSE_OK;
+}
+
+int check_device_error(bsechase_ctx *ctx) {
+    const int e = ctx->hsc->error;
+    if (e == DEV_OK) return BSE_OK;
+    const std::string where = std::to_string(ctx->hsc->error_where);
+    switch (e) {
+        case DEV_CHOL_FAIL:
+            return fail(ctx, BSE_ENONFINITE, "Cholesky factorisation failed at column %s",
+                        where.c_str());
+        case DEV_EIG_NOCONV:
+            return fail(ctx, BSE_ENONFINITE, "reduced eigensolver did not converge (%s)",
+                        where.c_str());
+        case DEV_NONFINITE:
+            return fail(ctx, BSE_ENONFINITE, "non-finite value in a reduction (column %s)",
+                        where.c_str());
+        default:
+            return fail(ctx, BSE_ECUDA, "device error %s", std::to_string(e).c_str());
+    }
+}
+
+int sync_scalars(bsechase_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->hsc, ctx->sc, sizeof(ChaseScalars), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return check_device_error(ctx);
+}
+
+// ---------------------------------------------------------------- phases
+
+// Lanczos estimate; results land in ctx->sc (beta, mu_1, mu_m, norm_est,
+// alpha = mu_m, lower = mu_1).
+int phase_lanczos(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int m, int steps,
+                  int runs, uint64_t seed) {
+    if (steps < 1 || steps > 64 || runs < 1 || runs > 8) return fail(ctx, BSE_EINVAL, "bad Lanczos size%s");
+    Small s = small_layout(ctx, m);
+    z_t *Vl = (z_t *)ctx->lz.p, *Vp = Vl + N * 8, *W = Vp + N * 8;
+    const int k = (int)std::min<int64_t>(steps, N);
+    CK(launch_random_block(seed, 4, N, runs, 0, Vl, N, ctx->st));
+    CK(launch_normalize_cols(N, runs, Vl, N, (double *)ctx->part.p, s.norms, ctx->sc, ctx->st));
+    CK(cudaMemsetAsync(Vp, 0, (size_t)N * runs * sizeof(z_t), ctx->st));
+    CK(cudaMemsetAsync(s.lz_beta, 0, 8 * sizeof(double), ctx->st));
+    GemmEpi plain{};
+    for (int j = 0; j < k; j++) {
+        CK(launch_zgemm_nn(N, runs, N, H, ldh, Vl, N, W, N, plain, ctx->st));
+        // beta_{j-1} (zeros before the first step) -> beta_j
+        const double *bprev = (j == 0) ? s.lz_beta : s.lz_beta + 8 + (j - 1) * runs;
+        CK(launch_lanczos_step(N, runs, Vl, Vp, W, N, s.lz_alpha + j * runs, bprev,
+                               s.lz_beta + 8 + j * runs, (double *)ctx->part.p, ctx->sc, ctx->st));
+    }
+    // beta history for the finaliser: row j of lz_beta + 8 holds beta_j
+    CK(launch_lanczos_finalize(k, runs, N, m, s.lz_alpha, s.lz_beta + 8, ctx->sc, ctx->st));
+    return BSE_OK;
+}
+
+// Filter columns V[:, 0..m) (degrees ascending, host copy h_deg, device copy
+// d_deg) in place; B1 is the second buffer of the recurrence.
+int phase_filter(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, z_t *V, int64_t ldv,
+                 int m, const int *h_deg, const int *d_deg, double lower, double c, double e,
+                 int64_t *matvecs, int64_t *launches = nullptr) {
+    if (m <= 0) return BSE_OK;
+    z_t *B1 = (z_t *)ctx->B1.p;
+    const int64_t ldb = N;
+    const double sigma1 = e / (lower - c);
+    GemmEpi ep{};
+    ep.mode = GEMM_CHEB;
+    ep.s1 = sigma1 / e;
+    ep.c = c;
+    ep.s2 = 0.0;
+    ep.Yp = nullptr;
+    // Y_1 = (sigma_1/e)(H Y_0 - c Y_0) into B1; Y_t lives in V (t even) or B1 (t odd)
+    CK(launch_zgemm_nn(N, m, N, H, ldh, V, ldv, B1, ldb, ep, ctx->st));
+    int64_t mv = m;
+    double sigma = sigma1;
+    const int dmax = h_deg[m - 1];
+    for (int t = 1; t < dmax; t++) {
+        int s = 0;
+        while (s < m && h_deg[s] <= t) s++;
+        const double sigma_new = 1.0 / (2.0 / sigma1 - sigma);
+        z_t *cur = (t & 1) ? B1 : V;
+        z_t *prv = (t & 1) ? V : B1;
+        const int64_t ldc = (t & 1) ? ldb : ldv, ldp = (t & 1) ? ldv : ldb;
+        ep.s1 = 2.0 * sigma_new / e;
+        ep.s2 = sigma * sigma_new;
+        ep.Yp = prv + s * ldp;
+        ep.ldyp = ldp;
+        CK(launch_zgemm_nn(N, m - s, N, H, ldh, cur + s * ldc, ldc, prv + s * ldp, ldp, ep,
+                           ctx->st));
+        mv += m - s;
+        sigma = sigma_new;
+    }
+    // column j's result Y_{d_j} is in B1 when d_j is odd
+    if (ldv != ldb) return fail(ctx, BSE_EINVAL, "filter block needs ld = N%s");
+    CK(launch_select_cols(N, m, V, B1, ldv, d_deg, 1, V, ctx->st));
+    if (matvecs) *matvecs = mv;
+    if (launches) *launches += dmax;
+    return BSE_OK;
+}
+
+// V -= L (L^H V)
+int project(bsechase_ctx *ctx, const z_t *L, int64_t ldl, int k, z_t *V, int64_t ldv, int64_t N,
+            int m) {
+    if (k <= 0) return BSE_OK;
+    z_t *X = (z_t *)ctx->R.p;
+    CK(launch_zgemm_cn(k, m, N, L, ldl, V, ldv, X, k, 0.0, 0, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    GemmEpi ep{};
+    ep.mode = GEMM_SUB;
+    ep.D = V;
+    ep.ldd = ldv;
+    CK(launch_zgemm_nn(N, m, k, L, ldl, X, k, V, ldv, ep, ctx->st));
+    return BSE_OK;
+}
+
+// one Cholesky QR pass: G = V^H V + shift I = R^H R, V <- V R^{-1}
+int cholqr_pass(bsechase_ctx *ctx, z_t *V, int64_t ldv, int64_t N, int m, double shift) {
+    z_t *G = (z_t *)ctx->G.p, *Ri = (z_t *)ctx->Ri.p, *B1 = (z_t *)ctx->B1.p;
+    CK(launch_zgemm_cn(m, m, N, V, ldv, V, ldv, G, m, shift, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    CK(launch_cholesky(m, G, m, ctx->sc, ctx->st));
+    CK(launch_trinv(m, G, m, Ri, m, ctx->st));
+    GemmEpi plain{};
+    CK(launch_zgemm_nn(N, m, m, V, ldv, Ri, m, B1, N, plain, ctx->st));
+    CK(launch_copy_cols(N, m, B1, N, V, ldv, nullptr, ctx->st));
+    return BSE_OK;
+}
+
+int phase_qr(bsechase_ctx *ctx, const z_t *L, int64_t ldl, int k, z_t *V, int64_t ldv, int64_t N,
+             int m) {
+    int rc;
+    if (m <= 0) return BSE_OK;
+    Small s = small_layout(ctx, m);
+    if ((rc = project(ctx, L, ldl, k, V, ldv, N, m))) return rc;
+    if ((rc = project(ctx, L, ldl, k, V, ldv, N, m))) return rc;
+    CK(launch_normalize_cols(N, m, V, ldv, (double *)ctx->part.p, s.norms, ctx->sc, ctx->st));
+    // columns have unit norm, so ||V||_F^2 = m
+    const double shift = 11.0 * ((double)N * m + (double)m * (m + 1)) * kU * (double)m;
+    if ((rc = cholqr_pass(ctx, V, ldv, N, m, shift))) return rc;
+    for (int pass = 0; pass < 2; pass++) {
+        if ((rc = project(ctx, L, ldl, k, V, ldv, N, m))) return rc;
+        if ((rc = cholqr_pass(ctx, V, ldv, N, m, 0.0))) return rc;
+    }
+    return BSE_OK;
+}
+
+// Rayleigh-Ritz: theta (device), Vout = Q Y (ld N), HVout = H Q Y (ld N)
+int phase_rr(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, const z_t *Q, int64_t ldq,
+             int m, double *theta, z_t *Vout, z_t *HVout) {
+    z_t *W = (z_t *)ctx->B1.p, *G = (z_t *)ctx->G.p, *Yr = (z_t *)ctx->Yr.p;
+    GemmEpi plain{};
+    CK(launch_zgemm_nn(N, m, N, H, ldh, Q, ldq, W, N, plain, ctx->st));
+    CK(launch_zgemm_cn(m, m, N, Q, ldq, W, N, G, m, 0.0, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    CK(launch_heev(m, G, m, theta, Yr, m, ctx->heev.p, ctx->sc, ctx->st));
+    CK(launch_zgemm_nn(N, m, m, Q, ldq, Yr, m, Vout, N, plain, ctx->st));
+    CK(launch_zgemm_nn(N, m, m, W, N, Yr, m, HVout, N, plain, ctx->st));
+    return BSE_OK;
+}
+
+struct Timer {
+    bsechase_ctx *ctx;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    void mark(int i) {
+        if (ctx->ev_ok) cudaEventRecord(ctx->ev[i], ctx->st);
+    }
+    void add(int phase, int a, int b) {
+        float ms = 0.f;
+        if (ctx->ev_ok && cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]) == cudaSuccess)
+            acc[phase] += ms;
+    }
+};
+
+int validate_solve(bsechase_ctx *ctx, const void *H, int64_t N, int64_t ldh, int nev, int nex,
+                   double tol, int deg_max, int precision, int64_t ldz) {
+    if (!ctx) return BSE_EINVAL;
+    if (!H) return fail(ctx, BSE_EINVAL, "H is NULL%s");
+    if (N < 1 || ldh < N || ldz < N) return fail(ctx, BSE_EINVAL, "bad N or leading dimension%s");
+    if (nev < 1 || nex < 0 || (int64_t)nev + nex > N || nev + nex > kMaxM)
+        return fail(ctx, BSE_EINVAL, "need 1 <= nev, 0 <= nex, nev + nex <= min(N, 512)%s");
+    if (!(tol > 0.0) || deg_max < 2) return fail(ctx, BSE_EINVAL, "need tol > 0 and deg_max >= 2%s");
+    if (precision != CHASE_FP64) return fail(ctx, BSE_EINVAL, "unsupported precision%s");
+    return BSE_OK;
+}
+
+int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
+                 double tol, int deg_max, const chase_opts *opts, double *h_evals, z_t *d_evecs,
+                 int64_t ldz, double *h_resid, chase_stats *stats) {
+    int rc;
+    const int m = nev + nex;
+    chase_opts o{};
+    o.deg_init = 20;
+    o.max_iter = 50;
+    o.lanczos_steps = 25;
+    o.lanczos_vecs = 4;
+    o.seed = 0;
+    if (opts) {
+        if (opts->deg_init > 0) o.deg_init = opts->deg_init;
+        if (opts->max_iter > 0) o.max_iter = opts->max_iter;
+        if (opts->lanczos_steps > 0) o.lanczos_steps = opts->lanczos_steps;
+        if (opts->lanczos_vecs > 0) o.lanczos_vecs = opts->lanczos_vecs;
+        o.seed = opts->seed;
+        o.d_V0 = opts->d_V0;
+        o.ldv0 = opts->ldv0;
+        o.n_v0 = opts->n_v0;
+    }
+    if (o.d_V0 && (o.n_v0 < 0 || o.ldv0 < N)) return fail(ctx, BSE_EINVAL, "bad warm-start block%s");
+    if ((rc = ensure_workspace(ctx, N, m))) return rc;
+    Small s = small_layout(ctx, m);
+    z_t *V = (z_t *)ctx->V.p, *B2 = (z_t *)ctx->B2.p, *B3 = (z_t *)ctx->B3.p;
+    Timer tm{ctx};
+    const int64_t launches0 = bse_launch_count();
+    tm.mark(0);
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    if ((rc = phase_lanczos(ctx, H, N, ldh, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
+    tm.mark(1);
+    int64_t matvecs = (int64_t)std::min<int64_t>(o.lanczos_steps, N) * o.lanczos_vecs;
+    int64_t filter_mv = 0, filter_launches = 0;
+    // start block: seeded columns, the first n_v0 replaced by the warm start
+    CK(launch_random_block(o.seed, 5, N, m, 0, V, N, ctx->st));
+    if (o.d_V0 && o.n_v0 > 0)
+        CK(launch_copy_cols(N, std::min(o.n_v0, m), (const z_t *)o.d_V0, o.ldv0, V, N, nullptr,
+                            ctx->st));
+    if ((rc = sync_scalars(ctx))) return rc;
+    tm.add(0, 0, 1);
+    double alpha = ctx->hsc->alpha, beta = ctx->hsc->beta, lower = ctx->hsc->lower;
+    const double norm_est = ctx->hsc->norm_est;
+    int d0 = std::min(o.deg_init + (o.deg_init & 1), deg_max);
+    std::vector<int> hdeg(m, d0);
+    CK(cudaMemcpyAsync(s.deg, hdeg.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    std::vector<double> lam(m, 0.0), res(m, INFINITY), th(m), rr(m);
+    std::vector<int> perm(m);
+    int locked = 0, it = 0;
+    bool converged = false;
+    while (it < o.max_iter) {
+        it++;
+        const int ma = m - locked;
+        const double c = (alpha + beta) / 2.0, e = (beta - alpha) / 2.0;
+        z_t *Va = V + (int64_t)locked * N;
+        tm.mark(2);
+        int64_t mv = 0;
+        if ((rc = phase_filter(ctx, H, N, ldh, Va, N, ma, hdeg.data(), s.deg, lower, c, e, &mv,
+                               &filter_launches)))
+            return rc;
+        filter_mv += mv;
+        tm.mark(3);
+        if ((rc = phase_qr(ctx, V, N, locked, Va, N, N, ma))) return rc;
+        tm.mark(4);
+        if ((rc = phase_rr(ctx, H, N, ldh, Va, N, ma, s.theta, B2, B3))) return rc;
+        matvecs += ma;
+        tm.mark(5);
+        CK(launch_residuals(N, ma, B3, N, B2, N, s.theta, s.resid, (double *)ctx->part.p, ctx->sc,
+                            ctx->st));
+        CK(launch_chase_update(ma, nev, tol, deg_max, s.theta, s.resid, s.deg, s.perm, ctx->sc,
+                               ctx->st));
+        CK(launch_copy_cols(N, ma, B2, N, Va, N, s.perm, ctx->st));
+        tm.mark(6);
+        CK(cudaMemcpyAsync(th.data(), s.theta, ma * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(rr.data(), s.resid, ma * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(perm.data(), s.perm, ma * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        CK(cudaMemcpyAsync(hdeg.data(), s.deg, ma * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+        if ((rc = sync_scalars(ctx))) return rc;
+        tm.add(1, 2, 3);
+        tm.add(2, 3, 4);
+        tm.add(3, 4, 5);
+        tm.add(4, 5, 6);
+        for (int j = 0; j < ma; j++) {
+            lam[locked + j] = th[perm[j]];
+            res[locked + j] = rr[perm[j]];
+        }
+        locked = ctx->hsc->locked;
+        alpha = ctx->hsc->alpha;
+        lower = ctx->hsc->lower;
+        if (locked >= nev) {
+            converged = true;
+            break;
+        }
+    }
+    // output: locked pairs sorted ascending
+    tm.mark(2);
+    std::vector<int> order(nev);
+    for (int j = 0; j < nev; j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+    for (int j = 0; j < nev; j++) {
+        h_evals[j] = lam[order[j]];
+        h_resid[j] = (order[j] < locked) ? res[order[j]] : INFINITY;
+    }
+    CK(cudaMemcpyAsync(s.order, order.data(), nev * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    CK(launch_copy_cols(N, nev, V, N, d_evecs, ldz, s.order, ctx->st));
+    CK(launch_phase_normalize(N, nev, d_evecs, ldz, ctx->st));
+    tm.mark(3);
+    CK(cudaStreamSynchronize(ctx->st));
+    tm.add(4, 2, 3);
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->iters = it;
+        stats->locked = locked;
+        stats->matvecs = matvecs + filter_mv;
+        stats->filter_matvecs = filter_mv;
+        stats->ms_lanczos = tm.acc[0];
+        stats->ms_filter = tm.acc[1];
+        stats->ms_qr = tm.acc[2];
+        stats->ms_rr = tm.acc[3];
+        stats->ms_resid = tm.acc[4];
+        stats->ms_total = tm.acc[0] + tm.acc[1] + tm.acc[2] + tm.acc[3] + tm.acc[4];
+        stats->filter_tflops =
+            (tm.acc[1] > 0) ? 8.0 * (double)N * (double)N * (double)filter_mv / (tm.acc[1] * 1e9)
+                            : 0.0;
+        stats->norm_est = norm_est;
+        stats->alpha = alpha;
+        stats->beta = beta;
+        stats->lower = lower;
+        stats->kernel_launches = bse_launch_count() - launches0;
+        stats->filter_launches = filter_launches;
+    }
+    if (!converged) return fail(ctx, BSE_ENOCONV, "not converged after max_iter iterations%s");
+    return BSE_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+const char *bsechase_strerror(int status) {
+    switch (status) {
+        case BSE_OK: return "success";
+        case BSE_EINVAL: return "invalid argument";
+        case BSE_ENOMEM: return "out of device memory";
+        case BSE_ENOCONV: return "not converged";
+        case BSE_ENONFINITE: return "non-finite value or failed factorisation";
+        case BSE_ETIMEOUT: return "timed out";
+        case BSE_ECUDA: return "CUDA error";
+        case BSE_EBUSY: return "busy";
+        default: return "unknown status";
+    }
+}
+
+const char *bsechase_last_error(const bsechase_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int bsechase_create(bsechase_ctx **out, int device, void *stream) {
+    if (!out) return BSE_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return BSE_ECUDA;
+    }
+    bsechase_ctx *ctx = new (std::nothrow) bsechase_ctx();
+    if (!ctx) return BSE_ENOMEM;
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (stream) {
+        ctx->st = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) == cudaSuccess) {
+        ctx->own_stream = true;
+    } else {
+        delete ctx;
+        return BSE_ECUDA;
+    }
+    if (cudaMalloc(&ctx->sc, sizeof(ChaseScalars)) != cudaSuccess ||
+        cudaMallocHost(&ctx->hsc, sizeof(ChaseScalars)) != cudaSuccess) {
+        bsechase_destroy(ctx);
+        return BSE_ENOMEM;
+    }
+    ctx->ev_ok = true;
+    for (int i = 0; i < 8; i++)
+        if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;
+    *out = ctx;
+    return BSE_OK;
+}
+
+void bsechase_destroy(bsechase_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
+                      &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
+                      &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev};
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->sc) cudaFree(ctx->sc);
+    if (ctx->hsc) cudaFreeHost(ctx->hsc);
+    for (int i = 0; i < 8; i++)
+        if (ctx->ev_ok) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->st);
+    delete ctx;
+}
+
+int64_t bse_dim(int Nk, int Nv, int Nc) {
+    if (Nk < 1 || Nv < 1 || Nc < 1) return -1;
+    const int64_t N = (int64_t)Nk * Nv * Nc;
+    return N > (int64_t)1 << 31 ? -1 : N;
+}
+
+int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
+                          const bse_model *model, void *d_H, int64_t ldh) {
+    if (!ctx) return BSE_EINVAL;
+    const int64_t N = bse_dim(Nk, Nv, Nc);
+    if (N < 1 || !d_H || ldh < N) return fail(ctx, BSE_EINVAL, "bad sizes or NULL H%s");
+    BseModel md{2.0, 0.3, 0.5, 0.01, 1.0, 8};
+    if (model) {
+        md.band_gap = model->band_gap;
+        md.w0 = model->w0;
+        md.x0 = model->x0;
+        md.jitter = model->jitter;
+        md.dispersion = model->dispersion;
+        md.rank_x = model->rank_x;
+    }
+    if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    const size_t tb = (size_t)N * (2 * sizeof(double) + std::max(md.rank_x, 1) * sizeof(z_t));
+    if ((rc = ensure(ctx, ctx->tables, tb))) return rc;
+    double *dE = (double *)ctx->tables.p, *theta = dE + N;
+    z_t *a = (z_t *)(theta + N);
+    CK(launch_bse_build(seed, Nk, Nv, Nc, md, dE, theta, a, (z_t *)d_H, ldh, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return BSE_OK;
+}
+
+int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int nev, int nex,
+                double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
+                void *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats) {
+    int rc = validate_solve(ctx, d_H, N, ldh, nev, nex, tol, deg_max, precision, ldz);
+    if (rc) return rc;
+    if (!h_evals || !d_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    return solve_device(ctx, (const z_t *)d_H, N, ldh, nev, nex, tol, deg_max, opts, h_evals,
+                        (z_t *)d_evecs, ldz, h_resid, stats);
+}
+
+int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh, int nev,
+                     int nex, double tol, int deg_max, int precision, const chase_opts *opts,
+                     double *h_evals, void *h_evecs, int64_t ldz, double *h_resid,
+                     chase_stats *stats) {
+    int rc = validate_solve(ctx, h_H, N, ldh, nev, nex, tol, deg_max, precision, ldz);
+    if (rc) return rc;
+    if (!h_evals || !h_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    if ((rc = ensure(ctx, ctx->Hdev, (size_t)N * N * sizeof(z_t)))) return rc;
+    if ((rc = ensure(ctx, ctx->Zdev, (size_t)N * nev * sizeof(z_t)))) return rc;
+    CK(cudaMemcpy2DAsync(ctx->Hdev.p, N * sizeof(z_t), h_H, ldh * sizeof(z_t), N * sizeof(z_t), N,
+                         cudaMemcpyHostToDevice, ctx->st));
+    rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max, opts, h_evals,
+                      (z_t *)ctx->Zdev.p, N, h_resid, stats);
+    if (rc != BSE_OK && rc != BSE_ENOCONV) return rc;
+    CK(cudaMemcpy2DAsync(h_evecs, ldz * sizeof(z_t), ctx->Zdev.p, N * sizeof(z_t), N * sizeof(z_t),
+                         nev, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return rc;
+}
+
+int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int m, int steps,
+                  int runs, uint64_t seed, double *out) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_H || !out || N < 1 || ldh < N || m < 1 || m > N)
+        return fail(ctx, BSE_EINVAL, "bad Lanczos arguments%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    if ((rc = ensure_workspace(ctx, N, std::min<int64_t>(m, kMaxM)))) return rc;
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    if ((rc = phase_lanczos(ctx, (const z_t *)d_H, N, ldh, m, steps, runs, seed))) return rc;
+    if ((rc = sync_scalars(ctx))) return rc;
+    out[0] = ctx->hsc->beta;
+    out[1] = ctx->hsc->mu_1;
+    out[2] = ctx->hsc->mu_m;
+    out[3] = ctx->hsc->norm_est;
+    return BSE_OK;
+}
+
+int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, void *d_V,
+                 int64_t ldv, int m, const int *h_deg, double lower, double c, double e,
+                 int64_t *matvecs) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_H || !d_V || !h_deg || N < 1 || ldh < N || ldv != N || m < 1 || m > kMaxM || !(e > 0))
+        return fail(ctx, BSE_EINVAL, "bad filter arguments (ldv must equal N)%s");
+    for (int j = 0; j < m; j++)
+        if (h_deg[j] < 1 || (j > 0 && h_deg[j] < h_deg[j - 1]))
+            return fail(ctx, BSE_EINVAL, "degrees must be >= 1 and ascending%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    if ((rc = ensure_workspace(ctx, N, m))) return rc;
+    Small s = small_layout(ctx, m);
+    CK(cudaMemcpyAsync(s.deg, h_deg, m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    if ((rc = phase_filter(ctx, (const z_t *)d_H, N, ldh, (z_t *)d_V, ldv, m, h_deg, s.deg, lower,
+                           c, e, matvecs)))
+        return rc;
+    CK(cudaStreamSynchronize(ctx->st));
+    return BSE_OK;
+}
+
+int chase_qr(bsechase_ctx *ctx, const void *d_L, int64_t ldl, int k, void *d_V, int64_t ldv,
+             int64_t N, int m) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_V || N < 1 || ldv < N || m < 1 || k < 0 || k + m > kMaxM || (k > 0 && (!d_L || ldl < N)))
+        return fail(ctx, BSE_EINVAL, "bad QR arguments%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    if ((rc = ensure_workspace(ctx, N, k + m))) return rc;
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    if ((rc = phase_qr(ctx, (const z_t *)d_L, ldl, k, (z_t *)d_V, ldv, N, m))) return rc;
+    return sync_scalars(ctx);
+}
+
+int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
+                        const void *d_Q, int64_t ldq, int m, double *h_theta, void *d_V,
+                        void *d_HV, double norm, double *h_resid) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_H || !d_Q || !h_theta || !d_V || !d_HV || N < 1 || ldh < N || ldq < N || m < 1 ||
+        m > kMaxM)
+        return fail(ctx, BSE_EINVAL, "bad Rayleigh-Ritz arguments%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    if ((rc = ensure_workspace(ctx, N, m))) return rc;
+    Small s = small_layout(ctx, m);
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    if ((rc = phase_rr(ctx, (const z_t *)d_H, N, ldh, (const z_t *)d_Q, ldq, m, s.theta,
+                       (z_t *)d_V, (z_t *)d_HV)))
+        return rc;
+    if (h_resid) {
+        ChaseScalars one{};
+        one.norm_est = norm;
+        CK(cudaMemcpyAsync(&ctx->sc->norm_est, &one.norm_est, sizeof(double),
+                           cudaMemcpyHostToDevice, ctx->st));
+        CK(launch_residuals(N, m, (const z_t *)d_HV, N, (const z_t *)d_V, N, s.theta, s.resid,
+                            (double *)ctx->part.p, ctx->sc, ctx->st));
+        CK(cudaMemcpyAsync(h_resid, s.resid, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    }
+    CK(cudaMemcpyAsync(h_theta, s.theta, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    return sync_scalars(ctx);
+}
+
+}  // extern "C"
+
+#include <atomic>
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+int64_t bse_launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void bse_count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

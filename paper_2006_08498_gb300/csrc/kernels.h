@@ -1,0 +1,91 @@
+// Internal launch interface between the host driver and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct BseModel {
+    double band_gap, w0, x0, jitter, dispersion;
+    int rank_x;
+};
+
+// ---- generator (gen.cu)
+cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+                             double *dE, double *theta, z_t *a, z_t *H, int64_t ldh,
+                             cudaStream_t st);
+
+// ---- dense products (zgemm.cu)
+enum GemmMode { GEMM_PLAIN = 0, GEMM_SUB = 1, GEMM_CHEB = 2 };
+struct GemmEpi {
+    int mode;
+    double s1, c, s2;      // CHEB: C = s1 (AB - c B[i,j]) - s2 Yp[i,j]
+    const z_t *Yp;         // CHEB: previous iterate (may alias C); null when s2 == 0
+    int64_t ldyp;
+    const z_t *D;          // SUB: C = D - AB (may alias C)
+    int64_t ldd;
+};
+// C[M x n] = epi(A[M x K] B[K x n]), all column-major FP64 complex.
+cudaError_t launch_zgemm_nn(int64_t M, int64_t n, int64_t K, const z_t *A, int64_t lda,
+                            const z_t *B, int64_t ldb, z_t *C, int64_t ldc, const GemmEpi &ep,
+                            cudaStream_t st);
+// G[m1 x m2] = A^H B (+ shift on the diagonal), A: K x m1, B: K x m2; split-K
+// partial sums in `work` (>= zgemm_cn_work_elems(..) elements), reduced in a
+// fixed order so the result is deterministic.
+int64_t zgemm_cn_work_elems(int64_t m1, int64_t m2, int64_t K);
+// The split count is reduced if ns * m1 * m2 would exceed work_elems.
+cudaError_t launch_zgemm_cn(int64_t m1, int64_t m2, int64_t K, const z_t *A, int64_t lda,
+                            const z_t *B, int64_t ldb, z_t *G, int64_t ldg, double shift,
+                            int hermitize, z_t *work, int64_t work_elems, cudaStream_t st);
+
+// ---- vector kernels (vec.cu)
+int vec_partial_blocks(int64_t N);
+// out[j] = sum_i |X[i,j]|^2 (sqrt if take_sqrt) for j < nc; partials in work
+cudaError_t launch_col_norms(int64_t N, int nc, const z_t *X, int64_t ldx, double *out,
+                             int take_sqrt, double *work, ChaseScalars *sc, cudaStream_t st);
+// X[:, j] *= 1/s[j]
+cudaError_t launch_col_inv_scale(int64_t N, int nc, z_t *X, int64_t ldx, const double *s,
+                                 cudaStream_t st);
+// r[j] = ||HV[:,j] - theta[j] V[:,j]|| / sc->norm_est
+cudaError_t launch_residuals(int64_t N, int nc, const z_t *HV, int64_t ldhv, const z_t *V,
+                             int64_t ldv, const double *theta, double *r, double *work,
+                             ChaseScalars *sc, cudaStream_t st);
+// out[:, j] = in[:, perm ? perm[j] : j]
+cudaError_t launch_copy_cols(int64_t N, int nc, const z_t *in, int64_t ldin, z_t *out,
+                             int64_t ldout, const int *perm, cudaStream_t st);
+// Seeded complex block (2u-1) + i(2u'-1) from SplitMix64, as in the generator
+cudaError_t launch_random_block(uint64_t seed, uint64_t stream, int64_t n, int m, int col0,
+                                z_t *V, int64_t ldv, cudaStream_t st);
+// Lanczos: per column l: a_l = Re(v_l^H w_l) (dots), then
+// w_l -= a_l v_l + b_l v_prev_l (b_l = beta_prev[l]), b'_l = ||w_l||,
+// v_prev <- v, v <- w / b'; a_l -> alpha_out[l], b'_l -> beta_out[l].
+cudaError_t launch_lanczos_step(int64_t N, int nl, z_t *V, z_t *Vprev, z_t *W, int64_t ld,
+                                double *alpha_out, const double *beta_prev, double *beta_out,
+                                double *work, ChaseScalars *sc, cudaStream_t st);
+// Unit phase making each column's largest-modulus entry real positive.
+cudaError_t launch_phase_normalize(int64_t N, int nc, z_t *X, int64_t ldx, cudaStream_t st);
+cudaError_t launch_normalize_cols(int64_t N, int nc, z_t *X, int64_t ldx, double *work,
+                                  double *norms, ChaseScalars *sc, cudaStream_t st);
+// out[:, j] = sel[j] ? B[:, j] : A[:, j]   (gather of filter results)
+cudaError_t launch_select_cols(int64_t N, int nc, const z_t *A, const z_t *B, int64_t ld,
+                               const int *deg, int parity, z_t *out, cudaStream_t st);
+
+// ---- single-CTA small dense kernels (small.cu)
+// In-place Cholesky G = R^H R (upper R, n x n); failure recorded in sc.
+cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st);
+// X = R^{-1} for upper-triangular R (n x n)
+cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, cudaStream_t st);
+// Eigen-decomposition of Hermitian A (n x n, destroyed): ascending w, vectors Y.
+size_t heev_work_bytes(int n);
+cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t ldy, void *work,
+                        ChaseScalars *sc, cudaStream_t st);
+// Lanczos estimates from the n_runs tridiagonals (alpha[k*nl + l], beta[k*nl + l]).
+cudaError_t launch_lanczos_finalize(int k, int nl, int64_t N, int m, const double *alpha,
+                                    const double *beta, ChaseScalars *sc, cudaStream_t st);
+// Locking, interval update, degrees and degree sort after a Rayleigh-Ritz step.
+// Inputs theta/resid of the m_act active pairs (ascending theta).  Outputs:
+// sc->new_locked / locked / alpha / lower, deg[0..m_act-nl) (ascending) and
+// perm (the Ritz index of each unlocked column after sorting).
+cudaError_t launch_chase_update(int m_act, int nev, double tol, int deg_max,
+                                const double *theta, const double *resid, int *deg, int *perm,
+                                ChaseScalars *sc, cudaStream_t st);

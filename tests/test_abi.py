@@ -1,0 +1,57 @@
+"""The C ABI library builds, loads and exports every symbol its header
+declares (no GPU needed: no compute calls are made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2006_08498_gb300 as pkg
+from paper_2006_08498_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M):
+            if not m.group(0).lstrip().startswith(("typedef", "#")):
+                names.append(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return pkg.load()
+
+
+def test_header_declares_expected_entry_points():
+    names = declared_functions()
+    assert set(names) == set(pkg.ABI_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(pkg.library_path())
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+
+
+def test_strerror_and_dim(lib):
+    assert lib.bsechase_strerror(0) == b"success"
+    assert lib.bsechase_strerror(-3) == b"not converged"
+    assert lib.bse_dim(125, 4, 4) == 2000
+    assert lib.bse_dim(3125, 4, 4) == 50000
+    assert lib.bse_dim(0, 4, 4) == -1
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.bse_build_hamiltonian(None, 0, 1, 1, 1, None, None, 1) == pkg.BSE_EINVAL
+    assert lib.chase_solve(None, None, 1, 1, 1, 0, 1e-10, 36, 0, None, None, None, 1,
+                           None, None) == pkg.BSE_EINVAL
+    lib.bsechase_destroy(None)  # ignored

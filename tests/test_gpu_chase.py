@@ -1,0 +1,323 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (complex FP64 path):
+  - generator: elementwise |dH| <= 4e-15 max|H| (the two sides differ only by
+    rounding of cos/sin/sqrt and FMA contraction);
+  - eigenvalues: relative error <= 1e-10; residuals ||Hv - lv||/||H||_2 <=
+    1e-9; subspace angles to the oracle's ChASE basis <= 1e-8 wherever the
+    nev cut does not split a cluster (gap > 1e-6 ||H||).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import block, degrees, hermitian, orthonormal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2006_08498_gb300 as pkg  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_08498_gb300 import build
+    build.build()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    """Column-major device copy of a numpy matrix."""
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a).T)).cuda()
+    return t.T
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def subspace_sin(A, B):
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    return float(np.linalg.norm(Qb - Qa @ (Qa.conj().T @ Qb), 2))
+
+
+# ------------------------------------------------------------- generator
+
+@pytest.mark.parametrize("shape,model", [
+    ((125, 4, 4), None),
+    ((7, 3, 5), None),                                    # ragged N = 105
+    ((24, 1, 1), dict(dispersion=0.0, jitter=0.0, x0=0.0)),
+    ((9, 2, 2), dict(rank_x=1, w0=0.0)),
+    ((5, 4, 3), dict(rank_x=0, w0=0.7, band_gap=3.0)),
+])
+def test_generator_matches_oracle(ctx, shape, model):
+    Nk, Nv, Nc = shape
+    Hd = ctx.build_hamiltonian(11, Nk, Nv, Nc, model)
+    Hg = host(Hd)
+    Ho = oracle.build_h(11, Nk, Nv, Nc, model)
+    assert np.array_equal(Hg, Hg.conj().T)                 # Hermitian bit for bit
+    assert np.all(np.diag(Hg).imag == 0)
+    assert np.max(np.abs(Hg - Ho)) <= 4e-15 * np.max(np.abs(Ho))
+
+
+def test_generator_leading_dimension(ctx):
+    N = 105
+    buf = torch.full((N, N + 7), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+    Hd = buf.T[:N, :]                   # N x N view of an (N+7) x N column-major buffer
+    ctx.build_hamiltonian(2, 7, 3, 5, out=Hd)
+    full = host(buf).T                  # (N+7) x N
+    assert np.all(full[N:, :] == 7.0)   # padding rows untouched
+    assert np.max(np.abs(full[:N, :] - oracle.build_h(2, 7, 3, 5))) <= 4e-15 * 12
+
+
+def test_generator_full_size_sampled(ctx):
+    """N = 20000 (Nk = 1250): sampled elements against the oracle evaluated
+    one by one, including the diagonal and the k-ring wrap-around."""
+    Nk, Nv, Nc = 1250, 4, 4
+    N = Nk * Nv * Nc
+    Hd = ctx.build_hamiltonian(0, Nk, Nv, Nc)
+    r = np.random.default_rng(1)
+    I = np.concatenate([r.integers(0, N, 4000), np.arange(0, N, 997), [N - 1, 0, N - 1, 16]])
+    J = np.concatenate([r.integers(0, N, 4000), np.arange(0, N, 997), [0, N - 1, N - 1, N - 16]])
+    # same band pair, far apart on the ring
+    I = np.concatenate([I, 16 * r.integers(0, Nk, 500) + 5])
+    J = np.concatenate([J, 16 * r.integers(0, Nk, 500) + 5])
+    ref = oracle.bse_elements(0, Nk, Nv, Nc, I, J)
+    got = Hd[torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 4e-15 * 12.0
+    mirror = Hd[torch.from_numpy(J).cuda(), torch.from_numpy(I).cuda()].cpu().numpy()
+    assert np.array_equal(mirror, got.conj())
+    del Hd
+    torch.cuda.empty_cache()
+
+
+# -------------------------------------------------------------- Lanczos
+
+def test_lanczos_matches_oracle(ctx):
+    H = oracle.build_h(0, 125, 4, 4)
+    est_o = oracle.lanczos_bounds(H, 75, seed=3)
+    est_g = ctx.lanczos(dev(H), 75, steps=25, runs=4, seed=3)
+    for key in ("beta", "mu_1", "norm_est"):
+        assert est_g[key] == pytest.approx(est_o[key], rel=1e-11)
+    assert est_g["mu_m"] == pytest.approx(est_o["mu_m"], rel=1e-8)
+
+
+# --------------------------------------------------------------- filter
+
+@pytest.mark.parametrize("n,m,seed", [(333, 7, 1), (257, 40, 2), (2000, 75, 3)])
+def test_filter_matches_oracle(ctx, n, m, seed):
+    if n == 2000:
+        A = oracle.build_h(0, 125, 4, 4)
+        lam = np.linalg.eigvalsh(A)
+    else:
+        A, lam = hermitian(n, seed)
+    V = block(n, m, seed + 10)
+    deg = degrees(m, seed + 20, 1, 36)
+    lower = lam[0]
+    c, e = oracle.filter_interval(lam[min(m, n - 1)], lam[-1] + 0.05)
+    Yo, mv_o = oracle.chebyshev_filter(A, V, deg, lower, c, e)
+    Vd = dev(V)
+    mv = ctx.filter(dev(A), Vd, deg, lower, c, e)
+    Yg = host(Vd)
+    assert mv == mv_o == int(np.sum(deg))
+    err = np.linalg.norm(Yg - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
+    assert np.max(err) <= 1e-11
+
+
+def test_filter_single_degree_closed_form(ctx):
+    """Diagonal H: each component is scaled by T_d((x-c)/e)/T_d((lower-c)/e)."""
+    n = 100
+    lam = np.linspace(0.5, 12.0, n)
+    V = block(n, 3, 4)
+    Vd = dev(V)
+    lower, c, e = 0.45, 8.0, 4.5
+    ctx.filter(dev(np.diag(lam).astype(complex)), Vd, [5, 5, 8], lower, c, e)
+    Y = host(Vd)
+
+    def T(d, x):
+        return math.cos(d * math.acos(x)) if abs(x) <= 1 else \
+            (1 if x > 0 or d % 2 == 0 else -1) * math.cosh(d * math.acosh(abs(x)))
+    for j, d in enumerate([5, 5, 8]):
+        s = np.array([T(d, (x - c) / e) / T(d, (lower - c) / e) for x in lam])
+        assert np.allclose(Y[:, j], s * V[:, j], rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------------- QR
+
+@pytest.mark.parametrize("n,k,m", [(300, 0, 17), (777, 9, 33), (2000, 40, 75)])
+def test_qr_matches_oracle(ctx, n, k, m):
+    L = orthonormal(n, k, 5) if k else None
+    X = block(n, m, 6)
+    # moderately ill-conditioned, with a large component along the locked block
+    U, _, Wh = np.linalg.svd(X, full_matrices=False)
+    X = (U * np.logspace(0, -4, m)) @ Wh
+    if k:
+        X = X + L @ block(k, m, 7)
+    Qo = oracle.qr(L, X)
+    Xd = dev(X)
+    ctx.qr(Xd, dev(L) if k else None)
+    Qg = host(Xd)
+    assert np.linalg.norm(Qg.conj().T @ Qg - np.eye(m)) <= 1e-13
+    if k:
+        assert np.linalg.norm(L.conj().T @ Qg) <= 1e-13
+    # Q of a QR with positive real R diagonal is unique: compare elementwise
+    assert np.max(np.abs(Qg - Qo)) <= 1e-9
+
+
+# ---------------------------------------------------------- Rayleigh-Ritz
+
+def test_rayleigh_ritz_matches_oracle(ctx):
+    A, lam = hermitian(500, 8)
+    Q = orthonormal(500, 30, 9)
+    th_o, V_o, HV_o = oracle.rayleigh_ritz(A, Q)
+    th_g, Vd, HVd, res = ctx.rayleigh_ritz(dev(A), dev(Q), norm=2.0)
+    V_g, HV_g = host(Vd), host(HVd)
+    assert np.allclose(th_g, th_o, rtol=1e-12, atol=1e-13)
+    assert np.allclose(res, oracle.residuals(HV_o, V_o, th_o, 2.0), rtol=1e-8, atol=1e-14)
+    # Ritz vectors agree up to a unit phase (distinct Ritz values)
+    for j in range(30):
+        ov = abs(np.vdot(V_o[:, j], V_g[:, j]))
+        assert ov == pytest.approx(1.0, abs=1e-10)
+    assert np.linalg.norm(A @ V_g - HV_g) <= 1e-12 * np.linalg.norm(HV_g)
+
+
+# ---------------------------------------------------------------- solve
+
+def _check_solution(H, evals, V, resid, nev, w_exact=None, ref=None):
+    normH = np.max(np.abs(np.linalg.eigvalsh(H))) if w_exact is None else np.max(np.abs(w_exact))
+    assert np.all(np.diff(evals) >= 0)
+    R = H @ V - V * evals
+    assert np.max(np.linalg.norm(R, axis=0)) / normH <= 1e-9
+    assert np.linalg.norm(V.conj().T @ V - np.eye(nev)) <= 1e-12
+    # phase convention: largest-modulus entry real positive
+    idx = np.argmax(np.abs(V), axis=0)
+    piv = V[idx, np.arange(nev)]
+    assert np.all(piv.real > 0) and np.all(piv.imag == 0)
+    if w_exact is not None:
+        assert np.max(np.abs(evals - w_exact[:nev]) / np.abs(w_exact[:nev])) <= 1e-10
+    if ref is not None:
+        gap = (w_exact[nev] - w_exact[nev - 1]) if w_exact is not None else 1.0
+        if gap > 1e-6 * normH:
+            assert subspace_sin(V, ref) <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def c1():
+    H = oracle.build_h(0, 125, 4, 4)
+    w, _ = oracle.eigh(H, 0)
+    ref = oracle.chase(H, 50, 25, tol=1e-10, deg_max=36)
+    return H, w, ref
+
+
+def test_solve_c1_matches_oracle(ctx, c1):
+    """N = 2000, nev = 50, nex = 25, tol 1e-10: against the dense oracle and
+    the oracle's own ChASE run with the same seeds."""
+    H, w, ref = c1
+    Hd = ctx.build_hamiltonian(0, 125, 4, 4)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36)
+    V = host(Vd)
+    _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
+    assert np.max(resid) <= 1e-10
+    assert np.allclose(evals, ref["evals"], rtol=1e-12, atol=0)
+    assert abs(st["iters"] - ref["iters"]) <= 1
+    assert st["iters"] >= 2
+
+
+def test_solve_is_deterministic(ctx):
+    Hd = ctx.build_hamiltonian(4, 30, 4, 4)
+    a = ctx.solve(Hd, 30, 15)
+    b = ctx.solve(Hd, 30, 15)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    assert torch.equal(a[1], b[1])
+    assert a[3]["matvecs"] == b[3]["matvecs"]
+
+
+@pytest.mark.parametrize("shape,nev,nex", [
+    ((7, 3, 5), 10, 7),        # ragged N = 105
+    ((3, 4, 4), 40, 8),        # m = N = 48
+    ((16, 4, 4), 1, 0),        # nev = 1, nex = 0
+    ((40, 4, 4), 100, 40),     # N = 640, m = 140
+])
+def test_solve_edge_shapes(ctx, shape, nev, nex):
+    Nk, Nv, Nc = shape
+    H = oracle.build_h(5, Nk, Nv, Nc)
+    w, _ = oracle.eigh(H, 0)
+    Hd = ctx.build_hamiltonian(5, Nk, Nv, Nc)
+    evals, Vd, resid, st = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36)
+    _check_solution(H, evals, host(Vd), resid, nev, w_exact=w)
+
+
+def test_solve_host_buffers_equal_device(ctx):
+    H = oracle.build_h(0, 30, 4, 4)
+    Hd = dev(H)
+    e1, V1, r1, _ = ctx.solve(Hd, 20, 10)
+    e2, V2, r2, _ = ctx.solve_host(np.asfortranarray(H), 20, 10)
+    assert np.array_equal(e1, e2) and np.array_equal(r1, r2)
+    assert np.array_equal(host(V1), V2)
+
+
+def test_warm_start_fewer_iterations(ctx):
+    Hd = ctx.build_hamiltonian(0, 40, 4, 4)
+    e1, V1, _, s1 = ctx.solve(Hd, 40, 20)
+    e2, _, _, s2 = ctx.solve(Hd, 40, 20, V0=V1)
+    assert s2["iters"] < s1["iters"]
+    assert np.allclose(e1, e2, rtol=1e-10, atol=0)
+
+
+def test_noconv_reports_inf(ctx):
+    Hd = ctx.build_hamiltonian(0, 16, 4, 4)
+    evals, _, resid, st = ctx.solve(Hd, 20, 10, max_iter=1, allow_noconv=True)
+    assert st["status"] == pkg.BSE_ENOCONV
+    assert np.all(np.isinf(resid))
+
+
+def test_invalid_arguments(ctx):
+    Hd = ctx.build_hamiltonian(0, 4, 2, 2)      # N = 16
+    bad = [dict(nev=0, nex=2), dict(nev=10, nex=10), dict(nev=4, nex=2, tol=0.0),
+           dict(nev=4, nex=2, deg_max=1), dict(nev=4, nex=2, precision=7)]
+    for kw in bad:
+        with pytest.raises(pkg.BseError) as ei:
+            ctx.solve(Hd, **kw)
+        assert ei.value.status == pkg.BSE_EINVAL
+
+
+def test_nonfinite_matrix_is_reported(ctx):
+    """A NaN planted in H (on the host side of the copy) is reported as
+    BSE_ENONFINITE, not returned as a result."""
+    H = oracle.build_h(0, 16, 4, 4)
+    H[3, 5] = np.nan
+    H[5, 3] = np.nan
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.solve(dev(H), 10, 5)
+    assert ei.value.status == pkg.BSE_ENONFINITE
+
+
+def test_solve_full_size_certified(ctx):
+    """N = 20000 (Nk = 1250), nev = 100, nex = 40, deg_max = 36, tol 1e-10:
+    the launch configuration of the benchmark.  Certified against the
+    oracle's matrix by properties that hold at any size: residuals
+    recomputed on the host (so, by Weyl's theorem, each eigenvalue is within
+    its residual of the spectrum), reported residuals, orthonormality."""
+    Nk, Nv, Nc, nev, nex = 1250, 4, 4, 100, 40
+    Hd = ctx.build_hamiltonian(0, Nk, Nv, Nc)
+    evals, Vd, resid, st = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36)
+    V = host(Vd)
+    del Hd
+    torch.cuda.empty_cache()
+    H = oracle.build_h(0, Nk, Nv, Nc)
+    R = H @ V - V * evals
+    normH = st["norm_est"]
+    rn = np.linalg.norm(R, axis=0)
+    assert np.max(rn) / normH <= 1e-9
+    assert np.allclose(rn / normH, resid, rtol=1e-3, atol=1e-13)
+    assert np.linalg.norm(V.conj().T @ V - np.eye(nev)) <= 1e-11
+    assert np.all(np.diff(evals) >= 0)
+    assert 2 <= st["iters"] <= 20
