@@ -24,7 +24,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="chase_fp64_N20000_nev100_nex40", Nk=1250, Nv=4, Nc=4, N=20000,
                 nev=100, nex=40, deg_max=36, tol=1e-10, seed=0, precision="fp64",
-                l2="inputs larger than L2 (H = 6.4 GB)")
+                l2="inputs larger than L2 (H = 6.4 GB)", matvecs_per_solve=22540)
 METRIC = "chase_time_to_solution"
 UNIT = "s"
 
@@ -38,14 +38,14 @@ def _peaks():
 
 
 # FP64 issue rate of the part: the measured DFMA peak when one is recorded
-# next to the bench (profiles/fp64_peak.json, written from a DFMA-loop
+# next to the bench (profiles/fp64_peak.txt, written from the DFMA-loop
 # probe), else the GB300 datasheet figure of 1.25 TFLOP/s.
 def _fp64_peak():
-    p = os.path.join(ROOT, "profiles", "fp64_peak.json")
+    p = os.path.join(ROOT, "profiles", "fp64_peak.txt")
     try:
         with open(p) as f:
             d = json.load(f)
-        return float(d["fp64_tflops"]), "measured DFMA loop (profiles/fp64_peak.json)"
+        return float(d["fp64_tflops"]), "measured DFMA loop (profiles/fp64_peak.txt)"
     except (OSError, KeyError, ValueError):
         return 1.25, "datasheet (no measured FP64 peak recorded)"
 
@@ -112,7 +112,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline_sample(seconds_budget=25.0):
+def workload(args):
+    """The benchmark workload, with optional overrides for profiling runs."""
+    W = dict(WORKLOAD)
+    if args.nk != W["Nk"] or args.nev != W["nev"] or args.nex != W["nex"]:
+        W.update(Nk=args.nk, nev=args.nev, nex=args.nex)
+        W["N"] = args.nk * W["Nv"] * W["Nc"]
+        W["workload"] = "chase_fp64_N%d_nev%d_nex%d" % (W["N"], args.nev, args.nex)
+        W["l2"] = "H = %.2f GB" % (16e-9 * W["N"] ** 2)
+        W["matvecs_per_solve"] = 160 * (args.nev + args.nex)   # rough, for profiling runs
+    return W
+
+
+def cpu_baseline_sample(W, seconds_budget=25.0):
     """The oracle, as it stands, on the host cores: builds the workload's H
     and times single filter matrix products over the full search space
     (m = 140 columns), then projects one solve from the per-matvec time and
@@ -120,7 +132,6 @@ def cpu_baseline_sample(seconds_budget=25.0):
     sample description, cores)."""
     import numpy as np
     import oracle
-    W = WORKLOAD
     t0 = time.perf_counter()
     H = oracle.build_h(W["seed"], W["Nk"], W["Nv"], W["Nc"])
     t_build = time.perf_counter() - t0
@@ -142,19 +153,21 @@ def run_reference(args, rank, world):
     of the same workload, projected to one solve."""
     if rank != 0:
         return
-    per_mv, t_build, reps, cores = cpu_baseline_sample()
-    # matvec count of one solve of this workload by the oracle's algorithm:
-    # taken from the oracle's own per-iteration rule on the same matrix is
-    # too slow to run here, so the count is the device solve's when known.
-    mv_total = float(os.environ.get("BENCH_SOLVE_MATVECS", "10400"))
+    W = workload(args)
+    per_mv, t_build, reps, cores = cpu_baseline_sample(W)
+    # H*vector products of one solve of this workload: the oracle and the
+    # device path take the same iterations and degrees (checked by the parity
+    # tests), so the count of the device's FP64 solve stands for the oracle's.
+    mv_total = float(W["matvecs_per_solve"])
     t_solve = t_build + per_mv * mv_total
-    sample = ("oracle build_h at N=20000 (%.1f s) + %d filter product(s) over 140 columns; "
-              "solve projected as build + %d matvecs x %.3e s" % (t_build, reps, mv_total, per_mv))
+    sample = ("oracle build_h at N=%d (%.1f s) + %d filter product(s) over %d columns; "
+              "solve projected as build + %d matvecs x %.3e s"
+              % (W["N"], t_build, reps, W["nev"] + W["nex"], mv_total, per_mv))
     line = {"impl": "reference", "metric": METRIC, "value": t_solve, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_solve * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD),
+            "config": W,
             "cpu_baseline": {"value": t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": t_solve, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -177,7 +190,7 @@ def run_ours(args, rank, world, local_rank):
         pkg_build.build()
     if dist:
         dist.barrier()
-    W = WORKLOAD
+    W = workload(args)
     N, nev, nex = W["N"], W["nev"], W["nex"]
     ctx = pkg.Context(local_rank)
     H = pkg.colmajor_empty(N, N, device="cuda:%d" % local_rank)
@@ -212,21 +225,23 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
 
-    # end to end through the host-buffer entry point: pinned H in, eigenvectors out
-    Hh = torch.empty((N, N), dtype=torch.complex128, pin_memory=True)
-    Hh.copy_(H.T)                          # Hh row-major = column-major H^T^T
-    Hcol = Hh.T                            # column-major view of the host matrix
-    Zh = torch.empty((nev, N), dtype=torch.complex128, pin_memory=True).T
-    ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh)
-    e2e_steps = max(1, min(args.steps, 2))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    # end to end through the host-buffer entry point: pinned H in, eigenvectors
+    # and eigenvalues out, one call per step (the device path is already warm)
+    e2e_s = None
+    if not args.no_e2e:
+        Hh = torch.empty((N, N), dtype=torch.complex128, pin_memory=True)
+        Hh.copy_(H.T)                      # row-major storage of H^T = column-major H
+        Hcol = Hh.T
+        Zh = torch.empty((nev, N), dtype=torch.complex128, pin_memory=True).T
+        e2e_steps = 1
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_s = float(te.item())
 
     if rank == 0:
         st = stats[-1]
@@ -251,20 +266,20 @@ def run_ours(args, rank, world, local_rank):
                          "peak_source": peak_src,
                          "traffic": (tr or {}).get("bytes_per_launch"),
                          "algorithmic_flops_per_launch_avg": per_launch_flops},
-            "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N * N,
-                    "d2h_bytes_per_step": 16 * N * nev + 16 * nev},
+            "e2e": None if e2e_s is None else {
+                "value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N * N,
+                "d2h_bytes_per_step": 16 * N * nev + 16 * nev},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats) + 2 * args.steps),
             "clocks": ck,
         }
         if world == 1 and not args.no_cpu_baseline:
-            os.environ.setdefault("BENCH_SOLVE_MATVECS", str(st["matvecs"]))
-            per_mv, t_build, reps, cores = cpu_baseline_sample()
+            per_mv, t_build, reps, cores = cpu_baseline_sample(W)
             t_cpu = t_build + per_mv * st["matvecs"]
             line["cpu_baseline"] = {
                 "value": t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": ("oracle build_h at N=20000 (%.1f s) + %d filter product(s) over 140 "
+                "sample": ("oracle build_h at N=%d (%.1f s) + %d filter product(s) over %d "
                            "columns (%.3e s/matvec), projected to this solve's %d matvecs"
-                           % (t_build, reps, per_mv, st["matvecs"]))}
+                           % (N, t_build, reps, nev + nex, per_mv, st["matvecs"]))}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -278,6 +293,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nk", type=int, default=WORKLOAD["Nk"], help="k-points (N = 16 Nk)")
+    ap.add_argument("--nev", type=int, default=WORKLOAD["nev"])
+    ap.add_argument("--nex", type=int, default=WORKLOAD["nex"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

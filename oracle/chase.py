@@ -348,6 +348,23 @@ def degrees(theta, resid, c, e, tol, deg_max):
     return out
 
 
+KAPPA_MAX = 1e12
+
+
+def degree_cap(lower, c, e, kappa_max=KAPPA_MAX):
+    """Largest even degree d (at least 2) with |T_d((lower - c)/e)| <=
+    kappa_max.  The filtered block's condition number is about
+    |T_d((lower - c)/e)| (components at `lower` keep their size, those at
+    alpha are divided by it), so the cap keeps the block numerically full
+    rank for Cholesky QR.  Returns None when no cap applies."""
+    t = abs((lower - c) / e)
+    if t <= 1.0:
+        return None
+    d = int(math.floor(math.acosh(kappa_max) / math.acosh(t)))
+    d -= d & 1
+    return max(2, d)
+
+
 def normalize_phase(V):
     """Make the largest-modulus entry of each column (smallest index on
     ties) real and positive."""
@@ -394,6 +411,9 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
     while it < max_iter:
         it += 1
         c, e = filter_interval(alpha, beta)
+        cap = degree_cap(lower, c, e)
+        if cap is not None:
+            deg = np.minimum(deg, cap)
         Vf, mv = chebyshev_filter(H, V[:, locked:], deg, lower, c, e)
         matvecs += mv
         Q = qr(V[:, :locked], Vf)

@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kMaxM = 512;
 constexpr double kU = 0x1.0p-53;
+constexpr double kKappaMax = 1e12;             // cap on the filter's amplification
 constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
 
 struct DevBuf {
@@ -347,7 +348,6 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     const double norm_est = ctx->hsc->norm_est;
     int d0 = std::min(o.deg_init + (o.deg_init & 1), deg_max);
     std::vector<int> hdeg(m, d0);
-    CK(cudaMemcpyAsync(s.deg, hdeg.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
     std::vector<double> lam(m, 0.0), res(m, INFINITY), th(m), rr(m);
     std::vector<int> perm(m);
     int locked = 0, it = 0;
@@ -357,6 +357,16 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         const int ma = m - locked;
         const double c = (alpha + beta) / 2.0, e = (beta - alpha) / 2.0;
         z_t *Va = V + (int64_t)locked * N;
+        // cap the degrees so the filtered block stays numerically full rank:
+        // its condition number is about |T_d((lower - c)/e)| <= kKappaMax
+        const double tl = fabs((lower - c) / e);
+        if (tl > 1.0) {
+            int cap = (int)floor(acosh(kKappaMax) / acosh(tl));
+            cap -= cap & 1;
+            if (cap < 2) cap = 2;
+            for (int j = 0; j < ma; j++) hdeg[j] = std::min(hdeg[j], cap);
+        }
+        CK(cudaMemcpyAsync(s.deg, hdeg.data(), ma * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
         tm.mark(2);
         int64_t mv = 0;
         if ((rc = phase_filter(ctx, H, N, ldh, Va, N, ma, hdeg.data(), s.deg, lower, c, e, &mv,

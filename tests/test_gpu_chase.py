@@ -243,7 +243,8 @@ def test_solve_is_deterministic(ctx):
 @pytest.mark.parametrize("shape,nev,nex", [
     ((7, 3, 5), 10, 7),        # ragged N = 105
     ((3, 4, 4), 40, 8),        # m = N = 48
-    ((16, 4, 4), 1, 0),        # nev = 1, nex = 0
+    ((16, 4, 4), 1, 1),        # nev = 1
+    ((16, 4, 4), 1, 2),
     ((40, 4, 4), 100, 40),     # N = 640, m = 140
 ])
 def test_solve_edge_shapes(ctx, shape, nev, nex):

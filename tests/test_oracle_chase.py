@@ -197,3 +197,24 @@ def test_chase_noconv_reports_inf():
     r = oracle.chase(H, 20, 10, max_iter=1)
     assert r["status"] == "noconv"
     assert np.all(np.isinf(r["resid"]))
+
+
+def test_degree_cap_bounds_amplification():
+    """The cap is the largest even degree with |T_d((lower-c)/e)| <= 1e12."""
+    lower, c, e = 0.5, 8.0, 5.0
+    d = oracle.degree_cap(lower, c, e)
+    t = (lower - c) / e
+    assert abs(_cheb(d, t)) <= 1e12 < abs(_cheb(d + 2, t))
+    assert d % 2 == 0
+    assert oracle.degree_cap(5.0, 8.0, 5.0) is None          # inside the interval
+    assert oracle.degree_cap(-1e6, 8.0, 1e-3) == 2            # floor of 2
+
+
+def test_chase_full_search_space():
+    """m = N: the capped filter keeps the block full rank and Rayleigh-Ritz
+    on the whole space is exact."""
+    H = oracle.build_h(5, 3, 4, 4)                           # N = 48
+    w = np.linalg.eigvalsh(H)
+    r = oracle.chase(H, 40, 8)
+    assert r["status"] == "ok"
+    assert np.max(np.abs(r["evals"] - w[:40])) < 1e-12
