@@ -22,7 +22,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="chase_fp64_N20000_nev100_nex40", Nk=1250, Nv=4, Nc=4, N=20000,
+WORKLOAD = dict(workload="chase_N20000_nev100_nex40", Nk=1250, Nv=4, Nc=4, N=20000,
                 nev=100, nex=40, deg_max=36, tol=1e-10, seed=0, precision="fp64",
                 l2="inputs larger than L2 (H = 6.4 GB)", matvecs_per_solve=22540)
 METRIC = "chase_time_to_solution"
@@ -50,8 +50,11 @@ def _fp64_peak():
         return 1.25, "datasheet (no measured FP64 peak recorded)"
 
 
-def _traffic():
-    p = os.path.join(ROOT, "profiles", "filter_traffic.json")
+def _traffic(precision):
+    """DRAM bytes per launch of the filter kernel from an ncu capture, when
+    profiles/filter_traffic_<precision>.txt records one for the current
+    kernel (JSON: {"bytes_per_launch": ...})."""
+    p = os.path.join(ROOT, "profiles", "filter_traffic_%s.txt" % precision)
     try:
         with open(p) as f:
             return json.load(f)
@@ -118,10 +121,49 @@ def workload(args):
     if args.nk != W["Nk"] or args.nev != W["nev"] or args.nex != W["nex"]:
         W.update(Nk=args.nk, nev=args.nev, nex=args.nex)
         W["N"] = args.nk * W["Nv"] * W["Nc"]
-        W["workload"] = "chase_fp64_N%d_nev%d_nex%d" % (W["N"], args.nev, args.nex)
+        W["workload"] = "chase_N%d_nev%d_nex%d" % (W["N"], args.nev, args.nex)
         W["l2"] = "H = %.2f GB" % (16e-9 * W["N"] ** 2)
         W["matvecs_per_solve"] = 160 * (args.nev + args.nex)   # rough, for profiling runs
     return W
+
+
+PRECISIONS = {"fp64": 0, "mixed": 1, "fp64_dfma": 2}
+DTYPES = {"fp64": "f64 (H products: bf16 slices on tensor cores, exact int + f32 accumulation)",
+          "mixed": "f64 with f32-level filter sweeps (bf16 slices, f32 accumulation)",
+          "fp64_dfma": "f64"}
+# slice-pair products per complex multiply-add of the tensor-core filter
+PAIRS = {"fp64": 21, "mixed": 6}
+
+
+def roofline(precision, st, N):
+    """Roofline of the dominant kernel (the filter's product), from the
+    library's CUDA-event filter time: FP64-equivalent work 8 N^2 per column
+    product; the tensor-core emulation executes 2 x 2 x 2 real flops per
+    complex multiply-add for each slice pair."""
+    peaks = _peaks()
+    fp64_eq = st["filter_tflops"]
+    tr = _traffic(precision)
+    if precision == "fp64_dfma":
+        peak, src = _fp64_peak()
+        return {"kernel": "zgemm_nn_kernel (filter H*Y, Chebyshev epilogue, DFMA)",
+                "bound": "alu", "achieved": fp64_eq, "peak": peak, "unit": "TFLOP/s",
+                "frac": fp64_eq / peak, "peak_source": src,
+                "traffic": (tr or {}).get("bytes_per_launch"),
+                "algorithmic_flops_per_launch_avg":
+                    8.0 * N * N * st["filter_matvecs"] / max(1, st["filter_launches"])}
+    low, hi = st["filter_matvecs_low"], st["filter_matvecs"] - st["filter_matvecs_low"]
+    pairs = (PAIRS["mixed"] * low + PAIRS["fp64"] * hi) / max(1, st["filter_matvecs"])
+    achieved = fp64_eq * pairs
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    return {"kernel": "k_ozaki_zgemm (filter H*Y, slice products on tcgen05, Chebyshev epilogue)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside "
+                            "a seconds-long solve)" if peaks else "fallback 1.7 PFLOP/s sustained"),
+            "traffic": (tr or {}).get("bytes_per_launch"),
+            "fp64_equivalent_tflops": fp64_eq, "slice_pairs_per_cmac": pairs,
+            "algorithmic_flops_per_launch_avg":
+                8.0 * pairs * N * N * st["filter_matvecs"] / max(1, st["filter_launches"])}
 
 
 def cpu_baseline_sample(W, seconds_budget=25.0):
@@ -197,9 +239,12 @@ def run_ours(args, rank, world, local_rank):
     evecs = pkg.colmajor_empty(N, nev, device="cuda:%d" % local_rank)
     stream = torch.cuda.current_stream()
 
+    prec = PRECISIONS[args.precision]
+
     def step():
         ctx.build_hamiltonian(W["seed"] + rank, W["Nk"], W["Nv"], W["Nc"], out=H)
-        return ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs)
+        return ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs,
+                         precision=prec)
 
     for _ in range(args.warmup):
         step()
@@ -236,7 +281,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_steps = 1
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh)
+            ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh,
+                           precision=prec)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         if dist:
@@ -246,26 +292,20 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         st = stats[-1]
         sec = ms_max / 1e3 / args.steps
-        fp64_peak, peak_src = _fp64_peak()
-        achieved = st["filter_tflops"]
-        tr = _traffic()
-        per_launch_flops = 8.0 * N * N * st["filter_matvecs"] / max(1, st["filter_launches"])
+        roof = roofline(args.precision, st, N)
         line = {
             "metric": METRIC, "value": sec, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": dict(W, parallelism="replicas" if world > 1 else "single"),
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": dict(W, precision=args.precision,
+                           parallelism="replicas" if world > 1 else "single"),
             "throughput_solves_per_s": world * args.steps / (ms_max / 1e3),
-            "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs", "ms_lanczos",
+            "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs",
+                                         "filter_matvecs_low", "filter_launches", "ms_lanczos",
                                          "ms_filter", "ms_qr", "ms_rr", "ms_resid",
                                          "ms_total", "filter_tflops")},
-            "roofline": {"kernel": "zgemm_nn_kernel (filter H*Y with Chebyshev epilogue)",
-                         "bound": "alu", "achieved": achieved, "peak": fp64_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                         "peak_source": peak_src,
-                         "traffic": (tr or {}).get("bytes_per_launch"),
-                         "algorithmic_flops_per_launch_avg": per_launch_flops},
+            "roofline": roof,
             "e2e": None if e2e_s is None else {
                 "value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N * N,
                 "d2h_bytes_per_step": 16 * N * nev + 16 * nev},
@@ -294,6 +334,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--nk", type=int, default=WORKLOAD["Nk"], help="k-points (N = 16 Nk)")
     ap.add_argument("--nev", type=int, default=WORKLOAD["nev"])
     ap.add_argument("--nex", type=int, default=WORKLOAD["nex"])

@@ -51,9 +51,21 @@ typedef enum {
 } bse_status;
 
 typedef enum {
-    CHASE_FP64 = 0,         /* every phase in FP64                            */
-    CHASE_MIXED_FP32 = 1    /* filter products in complex FP32, closing FP64
-                               sweeps; QR, Rayleigh-Ritz, residuals in FP64   */
+    CHASE_FP64 = 0,       /* FP64 accuracy.  Products with H (Lanczos, filter,
+                             Rayleigh-Ritz) run on the BF16 tensor cores as an
+                             Ozaki-scheme emulation: 6 slices of 8 bits per
+                             operand, exact integer accumulation of the
+                             leading slice products, FP32 for the rest (error
+                             ~1e-12 relative to |H||Y|).  QR, reduced eig,
+                             residuals and locking in native FP64.          */
+    CHASE_MIXED_FP32 = 1, /* filter products at FP32-level accuracy on the
+                             tensor cores (first 3 slices, FP32 accumulation)
+                             while every unlocked residual exceeds 1e-6, then
+                             FP64-accurate filter sweeps; Lanczos, QR,
+                             Rayleigh-Ritz and residuals as in CHASE_FP64.
+                             In single-phase entry points it selects the
+                             FP32-level product.                             */
+    CHASE_FP64_DFMA = 2   /* every product in native FP64 (DFMA)            */
 } chase_precision;
 
 /* Parameters of the synthetic Eq. (1) Hamiltonian (energies in eV).
@@ -91,6 +103,7 @@ typedef struct {
     double alpha, beta, lower; /* final damped interval and filter lower point */
     int64_t kernel_launches;   /* CUDA kernels this solve launched            */
     int64_t filter_launches;   /* filter matrix-product launches              */
+    int64_t filter_matvecs_low; /* filter products at FP32-level accuracy     */
 } chase_stats;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
@@ -149,7 +162,7 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
  * out[4] (host) = {beta (upper bound of lambda_N), mu_1 (estimate of
  * lambda_1), mu_m (estimate of lambda_m), ||H|| estimate}. */
 int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int m,
-                  int steps, int runs, uint64_t seed, double *out);
+                  int steps, int runs, uint64_t seed, int precision, double *out);
 
 /* Chebyshev filter (Sec. 3; Supplement, "Filter" item): column j of d_V
  * (N x m, ldv) is replaced by p_{d_j}(H) v_j, p_d(x) = T_d((x-c)/e) /
@@ -158,7 +171,7 @@ int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, in
  * in *matvecs (nullable). */
 int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, void *d_V,
                  int64_t ldv, int m, const int *h_deg, double lower, double c, double e,
-                 int64_t *matvecs);
+                 int precision, int64_t *matvecs);
 
 /* QR phase (Supplement, "QR" item): d_V (N x m) becomes an orthonormal
  * basis of span(d_V) projected off span(d_L) (d_L: N x k orthonormal, may
@@ -171,8 +184,22 @@ int chase_qr(bsechase_ctx *ctx, const void *d_L, int64_t ldl, int k, void *d_V, 
  * h_theta[m] ascending Ritz values; d_V = Q Y and d_HV = H Q Y (N x m,
  * ld = N); h_resid[m] = ||HV_j - theta_j V_j|| / norm (nullable). */
 int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
-                        const void *d_Q, int64_t ldq, int m, double *h_theta, void *d_V,
-                        void *d_HV, double norm, double *h_resid);
+                        const void *d_Q, int64_t ldq, int m, int precision, double *h_theta,
+                        void *d_V, void *d_HV, double norm, double *h_resid);
+
+/* Gram product of the QR and Rayleigh-Ritz phases (Supplement, "QR" and
+ * "RR" items): d_G (m1 x m2, ldg >= m1) = A^H B for A: K x m1 (lda), B: K x m2
+ * (ldb), 1 <= m1, m2 <= 512.  Split over K with a fixed partition and a
+ * fixed-order sum (run-to-run deterministic); partial sums live in the
+ * context's workspace. */
+int chase_gram(bsechase_ctx *ctx, const void *d_A, int64_t lda, const void *d_B, int64_t ldb,
+               int64_t K, int m1, int m2, void *d_G, int64_t ldg);
+
+/* The filter's matrix product alone: d_C = H d_Y (d_Y: N x n, ldy; d_C: N x n,
+ * ldc; 1 <= n <= 512) at the given precision (Sec. 3: the filter is a
+ * repeated HEMM).  d_C must not overlap d_H or d_Y. */
+int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
+               int64_t ldy, int n, void *d_C, int64_t ldc, int precision);
 
 #ifdef __cplusplus
 }

@@ -19,13 +19,14 @@ _LIBPATH = os.path.join(_HERE, "libbsechase.so")
 
 BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV = 0, -1, -2, -3
 BSE_ENONFINITE, BSE_ETIMEOUT, BSE_ECUDA, BSE_EBUSY = -4, -5, -6, -7
-CHASE_FP64, CHASE_MIXED_FP32 = 0, 1
+CHASE_FP64, CHASE_MIXED_FP32, CHASE_FP64_DFMA = 0, 1, 2
 
 # Every symbol include/bsechase.h declares.
 ABI_SYMBOLS = (
     "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
-    "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz",
+    "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
+    "chase_gram",
 )
 
 
@@ -57,7 +58,7 @@ class Stats(ctypes.Structure):
                 ("filter_tflops", ctypes.c_double), ("norm_est", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("lower", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("filter_launches", ctypes.c_int64)]
+                ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,15 +102,19 @@ def load():
     L.chase_solve.restype = i32
     L.chase_solve_host.argtypes = L.chase_solve.argtypes
     L.chase_solve_host.restype = i32
-    L.chase_lanczos.argtypes = [P, P, i64, i64, i32, i32, i32, u64, DP]
+    L.chase_lanczos.argtypes = [P, P, i64, i64, i32, i32, i32, u64, i32, DP]
     L.chase_lanczos.restype = i32
     L.chase_filter.argtypes = [P, P, i64, i64, P, i64, i32, ctypes.POINTER(ctypes.c_int),
-                               dbl, dbl, dbl, ctypes.POINTER(ctypes.c_int64)]
+                               dbl, dbl, dbl, i32, ctypes.POINTER(ctypes.c_int64)]
     L.chase_filter.restype = i32
     L.chase_qr.argtypes = [P, P, i64, i32, P, i64, i64, i32]
     L.chase_qr.restype = i32
-    L.chase_rayleigh_ritz.argtypes = [P, P, i64, i64, P, i64, i32, DP, P, P, dbl, DP]
+    L.chase_rayleigh_ritz.argtypes = [P, P, i64, i64, P, i64, i32, i32, DP, P, P, dbl, DP]
     L.chase_rayleigh_ritz.restype = i32
+    L.chase_hemm.argtypes = [P, P, i64, i64, P, i64, i32, P, i64, i32]
+    L.chase_hemm.restype = i32
+    L.chase_gram.argtypes = [P, P, i64, P, i64, i64, i32, i32, P, i64]
+    L.chase_gram.restype = i32
     _lib = L
     return L
 
@@ -262,21 +267,21 @@ class Context:
         return evals, evecs, resid, d
 
     # ------------------------------------------------------------- phases
-    def lanczos(self, H, m, steps=25, runs=4, seed=0):
+    def lanczos(self, H, m, steps=25, runs=4, seed=0, precision=CHASE_FP64):
         out = np.zeros(4)
         rc = load().chase_lanczos(self._h, ctypes.c_void_p(H.data_ptr()), H.shape[0], _ld(H),
-                                  m, steps, runs, seed, _dp(out))
+                                  m, steps, runs, seed, precision, _dp(out))
         self._check(rc)
         return dict(beta=out[0], mu_1=out[1], mu_m=out[2], norm_est=out[3])
 
-    def filter(self, H, V, degrees, lower, c, e):
+    def filter(self, H, V, degrees, lower, c, e, precision=CHASE_FP64):
         """In-place Chebyshev filter of the columns of V (ld must equal N)."""
         deg = np.ascontiguousarray(degrees, dtype=np.int32)
         mv = ctypes.c_int64(0)
         rc = load().chase_filter(self._h, ctypes.c_void_p(H.data_ptr()), H.shape[0], _ld(H),
                                  ctypes.c_void_p(V.data_ptr()), _ld(V), V.shape[1],
                                  deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), lower, c, e,
-                                 ctypes.byref(mv))
+                                 precision, ctypes.byref(mv))
         self._check(rc)
         return mv.value
 
@@ -288,14 +293,36 @@ class Context:
         self._check(rc)
         return V
 
-    def rayleigh_ritz(self, H, Q, norm=1.0):
+    def hemm(self, H, Y, precision=CHASE_FP64, out=None):
+        """C = H Y (the filter's product) as a new column-major tensor."""
+        N, n = Y.shape
+        C = colmajor_empty(N, n, device=Y.device) if out is None else out
+        rc = load().chase_hemm(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H),
+                               ctypes.c_void_p(Y.data_ptr()), _ld(Y), n,
+                               ctypes.c_void_p(C.data_ptr()), _ld(C), precision)
+        self._check(rc)
+        return C
+
+    def gram(self, A, B, out=None):
+        """G = A^H B (m1 x m2, column-major) for tall A (K x m1), B (K x m2)."""
+        K, m1 = A.shape
+        m2 = B.shape[1]
+        G = colmajor_empty(m1, m2, device=A.device) if out is None else out
+        rc = load().chase_gram(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
+                               ctypes.c_void_p(B.data_ptr()), _ld(B), K, m1, m2,
+                               ctypes.c_void_p(G.data_ptr()), _ld(G))
+        self._check(rc)
+        return G
+
+    def rayleigh_ritz(self, H, Q, norm=1.0, precision=CHASE_FP64):
         N, m = Q.shape
         theta = np.zeros(m)
         resid = np.zeros(m)
         V = colmajor_empty(N, m, device=Q.device)
         HV = colmajor_empty(N, m, device=Q.device)
         rc = load().chase_rayleigh_ritz(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H),
-                                        ctypes.c_void_p(Q.data_ptr()), _ld(Q), m, _dp(theta),
+                                        ctypes.c_void_p(Q.data_ptr()), _ld(Q), m, precision,
+                                        _dp(theta),
                                         ctypes.c_void_p(V.data_ptr()),
                                         ctypes.c_void_p(HV.data_ptr()), norm, _dp(resid))
         self._check(rc)

@@ -24,6 +24,9 @@ namespace {
 constexpr int kMaxM = 512;
 constexpr double kU = 0x1.0p-53;
 constexpr double kKappaMax = 1e12;             // cap on the filter's amplification
+// Mixed precision: the FP32-level filter is used while every unlocked pair's
+// residual is above this value; FP64-accurate sweeps close the solve.
+constexpr double kMixedSwitch = 1e-6;
 constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
 
 struct DevBuf {
@@ -42,6 +45,8 @@ struct bsechase_ctx {
     ChaseScalars *hsc = nullptr;     // pinned host mirror
     // workspace
     DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
+    DevBuf ozA, ozE, ozB, ozF;       // tensor-core products: slices of H and of the operand
+    OzakiH oh;
     int64_t wsN = 0;
     int wsM = 0;
     cudaEvent_t ev[8];
@@ -140,6 +145,9 @@ int check_device_error(bsechase_ctx *ctx) {
         case DEV_NONFINITE:
             return fail(ctx, BSE_ENONFINITE, "non-finite value in a reduction (column %s)",
                         where.c_str());
+        case DEV_TIMEOUT:
+            return fail(ctx, BSE_ETIMEOUT, "a bounded wait in a tensor-core kernel expired (CTA %s)",
+                        where.c_str());
         default:
             return fail(ctx, BSE_ECUDA, "device error %s", std::to_string(e).c_str());
     }
@@ -151,12 +159,55 @@ int sync_scalars(bsechase_ctx *ctx) {
     return check_device_error(ctx);
 }
 
+// ------------------------------------------------------- the operator H
+// Every product with H goes through Hop: native FP64 (zgemm.cu) or the
+// FP64-accurate tensor-core emulation (ozaki.cu), fixed per solve.
+struct Hop {
+    const z_t *H;
+    int64_t N, ldh;
+    bool tc;         // tensor-core emulation
+    bool low = false;  // FP32-level accuracy (mixed precision filter)
+};
+
+int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
+    if (!op.tc) return BSE_OK;
+    int rc;
+    const int64_t Np = ozaki_padded(op.N);
+    if ((rc = ensure(ctx, ctx->ozA, ozaki_a_bytes(op.N)))) return rc;
+    if ((rc = ensure(ctx, ctx->ozE, (size_t)Np * sizeof(int)))) return rc;
+    const int mc = std::max(max_cols, 32);
+    if ((rc = ensure(ctx, ctx->ozB, ozaki_b_bytes(op.N, mc)))) return rc;
+    if ((rc = ensure(ctx, ctx->ozF, (size_t)(mc + 64) * sizeof(int)))) return rc;
+    ctx->oh.A = ctx->ozA.p;
+    ctx->oh.E = (int *)ctx->ozE.p;
+    CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->st));
+    return BSE_OK;
+}
+
+// C[N x n] = epi(H Y)
+int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy, z_t *C,
+              int64_t ldc, const GemmEpi &ep) {
+    if (op.tc)
+        CK(ozaki_zgemm(ctx->oh, n, Y, ldy, C, ldc, ep, ctx->ozB.p, (int *)ctx->ozF.p, ctx->sc,
+                       op.low ? 1 : 0, ctx->st));
+    else
+        CK(launch_zgemm_nn(op.N, n, op.N, op.H, op.ldh, Y, ldy, C, ldc, ep, ctx->st));
+    return BSE_OK;
+}
+
+bool precision_uses_tc(int precision) {
+    return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32;
+}
+bool precision_valid(int precision) {
+    return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32 || precision == CHASE_FP64_DFMA;
+}
+
 // ---------------------------------------------------------------- phases
 
 // Lanczos estimate; results land in ctx->sc (beta, mu_1, mu_m, norm_est,
 // alpha = mu_m, lower = mu_1).
-int phase_lanczos(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int m, int steps,
-                  int runs, uint64_t seed) {
+int phase_lanczos(bsechase_ctx *ctx, const Hop &op, int m, int steps, int runs, uint64_t seed) {
+    const int64_t N = op.N;
     if (steps < 1 || steps > 64 || runs < 1 || runs > 8) return fail(ctx, BSE_EINVAL, "bad Lanczos size%s");
     Small s = small_layout(ctx, m);
     z_t *Vl = (z_t *)ctx->lz.p, *Vp = Vl + N * 8, *W = Vp + N * 8;
@@ -167,7 +218,8 @@ int phase_lanczos(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int m
     CK(cudaMemsetAsync(s.lz_beta, 0, 8 * sizeof(double), ctx->st));
     GemmEpi plain{};
     for (int j = 0; j < k; j++) {
-        CK(launch_zgemm_nn(N, runs, N, H, ldh, Vl, N, W, N, plain, ctx->st));
+        int rc;
+        if ((rc = hop_apply(ctx, op, runs, Vl, N, W, N, plain))) return rc;
         // beta_{j-1} (zeros before the first step) -> beta_j
         const double *bprev = (j == 0) ? s.lz_beta : s.lz_beta + 8 + (j - 1) * runs;
         CK(launch_lanczos_step(N, runs, Vl, Vp, W, N, s.lz_alpha + j * runs, bprev,
@@ -180,10 +232,12 @@ int phase_lanczos(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int m
 
 // Filter columns V[:, 0..m) (degrees ascending, host copy h_deg, device copy
 // d_deg) in place; B1 is the second buffer of the recurrence.
-int phase_filter(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, z_t *V, int64_t ldv,
-                 int m, const int *h_deg, const int *d_deg, double lower, double c, double e,
-                 int64_t *matvecs, int64_t *launches = nullptr) {
+int phase_filter(bsechase_ctx *ctx, const Hop &op, z_t *V, int64_t ldv, int m, const int *h_deg,
+                 const int *d_deg, double lower, double c, double e, int64_t *matvecs,
+                 int64_t *launches = nullptr) {
     if (m <= 0) return BSE_OK;
+    const int64_t N = op.N;
+    int rc;
     z_t *B1 = (z_t *)ctx->B1.p;
     const int64_t ldb = N;
     const double sigma1 = e / (lower - c);
@@ -194,7 +248,7 @@ int phase_filter(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, z_t *V
     ep.s2 = 0.0;
     ep.Yp = nullptr;
     // Y_1 = (sigma_1/e)(H Y_0 - c Y_0) into B1; Y_t lives in V (t even) or B1 (t odd)
-    CK(launch_zgemm_nn(N, m, N, H, ldh, V, ldv, B1, ldb, ep, ctx->st));
+    if ((rc = hop_apply(ctx, op, m, V, ldv, B1, ldb, ep))) return rc;
     int64_t mv = m;
     double sigma = sigma1;
     const int dmax = h_deg[m - 1];
@@ -209,8 +263,7 @@ int phase_filter(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, z_t *V
         ep.s2 = sigma * sigma_new;
         ep.Yp = prv + s * ldp;
         ep.ldyp = ldp;
-        CK(launch_zgemm_nn(N, m - s, N, H, ldh, cur + s * ldc, ldc, prv + s * ldp, ldp, ep,
-                           ctx->st));
+        if ((rc = hop_apply(ctx, op, m - s, cur + s * ldc, ldc, prv + s * ldp, ldp, ep))) return rc;
         mv += m - s;
         sigma = sigma_new;
     }
@@ -267,11 +320,13 @@ int phase_qr(bsechase_ctx *ctx, const z_t *L, int64_t ldl, int k, z_t *V, int64_
 }
 
 // Rayleigh-Ritz: theta (device), Vout = Q Y (ld N), HVout = H Q Y (ld N)
-int phase_rr(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, const z_t *Q, int64_t ldq,
-             int m, double *theta, z_t *Vout, z_t *HVout) {
+int phase_rr(bsechase_ctx *ctx, const Hop &op, const z_t *Q, int64_t ldq, int m, double *theta,
+             z_t *Vout, z_t *HVout) {
+    const int64_t N = op.N;
     z_t *W = (z_t *)ctx->B1.p, *G = (z_t *)ctx->G.p, *Yr = (z_t *)ctx->Yr.p;
     GemmEpi plain{};
-    CK(launch_zgemm_nn(N, m, N, H, ldh, Q, ldq, W, N, plain, ctx->st));
+    int rc;
+    if ((rc = hop_apply(ctx, op, m, Q, ldq, W, N, plain))) return rc;
     CK(launch_zgemm_cn(m, m, N, Q, ldq, W, N, G, m, 0.0, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
     CK(launch_heev(m, G, m, theta, Yr, m, ctx->heev.p, ctx->sc, ctx->st));
     CK(launch_zgemm_nn(N, m, m, Q, ldq, Yr, m, Vout, N, plain, ctx->st));
@@ -300,13 +355,13 @@ int validate_solve(bsechase_ctx *ctx, const void *H, int64_t N, int64_t ldh, int
     if (nev < 1 || nex < 0 || (int64_t)nev + nex > N || nev + nex > kMaxM)
         return fail(ctx, BSE_EINVAL, "need 1 <= nev, 0 <= nex, nev + nex <= min(N, 512)%s");
     if (!(tol > 0.0) || deg_max < 2) return fail(ctx, BSE_EINVAL, "need tol > 0 and deg_max >= 2%s");
-    if (precision != CHASE_FP64) return fail(ctx, BSE_EINVAL, "unsupported precision%s");
+    if (!precision_valid(precision)) return fail(ctx, BSE_EINVAL, "unsupported precision%s");
     return BSE_OK;
 }
 
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
-                 double tol, int deg_max, const chase_opts *opts, double *h_evals, z_t *d_evecs,
-                 int64_t ldz, double *h_resid, chase_stats *stats) {
+                 double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
+                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats) {
     int rc;
     const int m = nev + nex;
     chase_opts o{};
@@ -333,10 +388,12 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     const int64_t launches0 = bse_launch_count();
     tm.mark(0);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
-    if ((rc = phase_lanczos(ctx, H, N, ldh, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
+    Hop op{H, N, ldh, precision_uses_tc(precision)};
+    if ((rc = hop_prepare(ctx, op, m))) return rc;
+    if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
     tm.mark(1);
     int64_t matvecs = (int64_t)std::min<int64_t>(o.lanczos_steps, N) * o.lanczos_vecs;
-    int64_t filter_mv = 0, filter_launches = 0;
+    int64_t filter_mv = 0, filter_launches = 0, filter_mv_low = 0;
     // start block: seeded columns, the first n_v0 replaced by the warm start
     CK(launch_random_block(o.seed, 5, N, m, 0, V, N, ctx->st));
     if (o.d_V0 && o.n_v0 > 0)
@@ -369,14 +426,21 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         CK(cudaMemcpyAsync(s.deg, hdeg.data(), ma * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
         tm.mark(2);
         int64_t mv = 0;
-        if ((rc = phase_filter(ctx, H, N, ldh, Va, N, ma, hdeg.data(), s.deg, lower, c, e, &mv,
+        Hop fop = op;
+        if (precision == CHASE_MIXED_FP32) {
+            double rmin = INFINITY;
+            for (int j = locked; j < m; j++) rmin = std::min(rmin, res[j]);
+            fop.low = rmin > kMixedSwitch;
+        }
+        if ((rc = phase_filter(ctx, fop, Va, N, ma, hdeg.data(), s.deg, lower, c, e, &mv,
                                &filter_launches)))
             return rc;
         filter_mv += mv;
+        if (fop.low) filter_mv_low += mv;
         tm.mark(3);
         if ((rc = phase_qr(ctx, V, N, locked, Va, N, N, ma))) return rc;
         tm.mark(4);
-        if ((rc = phase_rr(ctx, H, N, ldh, Va, N, ma, s.theta, B2, B3))) return rc;
+        if ((rc = phase_rr(ctx, op, Va, N, ma, s.theta, B2, B3))) return rc;
         matvecs += ma;
         tm.mark(5);
         CK(launch_residuals(N, ma, B3, N, B2, N, s.theta, s.resid, (double *)ctx->part.p, ctx->sc,
@@ -442,6 +506,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         stats->lower = lower;
         stats->kernel_launches = bse_launch_count() - launches0;
         stats->filter_launches = filter_launches;
+        stats->filter_matvecs_low = filter_mv_low;
     }
     if (!converged) return fail(ctx, BSE_ENOCONV, "not converged after max_iter iterations%s");
     return BSE_OK;
@@ -518,7 +583,8 @@ void bsechase_destroy(bsechase_ctx *ctx) {
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
                       &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
-                      &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev};
+                      &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
+                      &ctx->ozB, &ctx->ozF};
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->sc) cudaFree(ctx->sc);
@@ -569,8 +635,8 @@ int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int 
     if (!h_evals || !d_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
     DeviceGuard g(ctx->device);
     ctx->err.clear();
-    return solve_device(ctx, (const z_t *)d_H, N, ldh, nev, nex, tol, deg_max, opts, h_evals,
-                        (z_t *)d_evecs, ldz, h_resid, stats);
+    return solve_device(ctx, (const z_t *)d_H, N, ldh, nev, nex, tol, deg_max, precision, opts,
+                        h_evals, (z_t *)d_evecs, ldz, h_resid, stats);
 }
 
 int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh, int nev,
@@ -586,8 +652,8 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
     if ((rc = ensure(ctx, ctx->Zdev, (size_t)N * nev * sizeof(z_t)))) return rc;
     CK(cudaMemcpy2DAsync(ctx->Hdev.p, N * sizeof(z_t), h_H, ldh * sizeof(z_t), N * sizeof(z_t), N,
                          cudaMemcpyHostToDevice, ctx->st));
-    rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max, opts, h_evals,
-                      (z_t *)ctx->Zdev.p, N, h_resid, stats);
+    rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max, precision, opts,
+                      h_evals, (z_t *)ctx->Zdev.p, N, h_resid, stats);
     if (rc != BSE_OK && rc != BSE_ENOCONV) return rc;
     CK(cudaMemcpy2DAsync(h_evecs, ldz * sizeof(z_t), ctx->Zdev.p, N * sizeof(z_t), N * sizeof(z_t),
                          nev, cudaMemcpyDeviceToHost, ctx->st));
@@ -596,15 +662,19 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
 }
 
 int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int m, int steps,
-                  int runs, uint64_t seed, double *out) {
+                  int runs, uint64_t seed, int precision, double *out) {
     if (!ctx) return BSE_EINVAL;
-    if (!d_H || !out || N < 1 || ldh < N || m < 1 || m > N)
+    if (!d_H || !out || N < 1 || ldh < N || m < 1 || m > N ||
+        !precision_valid(precision))
         return fail(ctx, BSE_EINVAL, "bad Lanczos arguments%s");
     DeviceGuard g(ctx->device);
     int rc;
     if ((rc = ensure_workspace(ctx, N, std::min<int64_t>(m, kMaxM)))) return rc;
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
-    if ((rc = phase_lanczos(ctx, (const z_t *)d_H, N, ldh, m, steps, runs, seed))) return rc;
+    Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
+           precision == CHASE_MIXED_FP32};
+    if ((rc = hop_prepare(ctx, op, 8))) return rc;
+    if ((rc = phase_lanczos(ctx, op, m, steps, runs, seed))) return rc;
     if ((rc = sync_scalars(ctx))) return rc;
     out[0] = ctx->hsc->beta;
     out[1] = ctx->hsc->mu_1;
@@ -615,9 +685,10 @@ int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, in
 
 int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, void *d_V,
                  int64_t ldv, int m, const int *h_deg, double lower, double c, double e,
-                 int64_t *matvecs) {
+                 int precision, int64_t *matvecs) {
     if (!ctx) return BSE_EINVAL;
-    if (!d_H || !d_V || !h_deg || N < 1 || ldh < N || ldv != N || m < 1 || m > kMaxM || !(e > 0))
+    if (!d_H || !d_V || !h_deg || N < 1 || ldh < N || ldv != N || m < 1 || m > kMaxM || !(e > 0) ||
+        !precision_valid(precision))
         return fail(ctx, BSE_EINVAL, "bad filter arguments (ldv must equal N)%s");
     for (int j = 0; j < m; j++)
         if (h_deg[j] < 1 || (j > 0 && h_deg[j] < h_deg[j - 1]))
@@ -627,11 +698,13 @@ int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, voi
     if ((rc = ensure_workspace(ctx, N, m))) return rc;
     Small s = small_layout(ctx, m);
     CK(cudaMemcpyAsync(s.deg, h_deg, m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
-    if ((rc = phase_filter(ctx, (const z_t *)d_H, N, ldh, (z_t *)d_V, ldv, m, h_deg, s.deg, lower,
-                           c, e, matvecs)))
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
+           precision == CHASE_MIXED_FP32};
+    if ((rc = hop_prepare(ctx, op, m))) return rc;
+    if ((rc = phase_filter(ctx, op, (z_t *)d_V, ldv, m, h_deg, s.deg, lower, c, e, matvecs)))
         return rc;
-    CK(cudaStreamSynchronize(ctx->st));
-    return BSE_OK;
+    return sync_scalars(ctx);
 }
 
 int chase_qr(bsechase_ctx *ctx, const void *d_L, int64_t ldl, int k, void *d_V, int64_t ldv,
@@ -648,19 +721,21 @@ int chase_qr(bsechase_ctx *ctx, const void *d_L, int64_t ldl, int k, void *d_V, 
 }
 
 int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
-                        const void *d_Q, int64_t ldq, int m, double *h_theta, void *d_V,
-                        void *d_HV, double norm, double *h_resid) {
+                        const void *d_Q, int64_t ldq, int m, int precision, double *h_theta,
+                        void *d_V, void *d_HV, double norm, double *h_resid) {
     if (!ctx) return BSE_EINVAL;
     if (!d_H || !d_Q || !h_theta || !d_V || !d_HV || N < 1 || ldh < N || ldq < N || m < 1 ||
-        m > kMaxM)
+        m > kMaxM || !precision_valid(precision))
         return fail(ctx, BSE_EINVAL, "bad Rayleigh-Ritz arguments%s");
     DeviceGuard g(ctx->device);
     int rc;
     if ((rc = ensure_workspace(ctx, N, m))) return rc;
     Small s = small_layout(ctx, m);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
-    if ((rc = phase_rr(ctx, (const z_t *)d_H, N, ldh, (const z_t *)d_Q, ldq, m, s.theta,
-                       (z_t *)d_V, (z_t *)d_HV)))
+    Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
+           precision == CHASE_MIXED_FP32};
+    if ((rc = hop_prepare(ctx, op, m))) return rc;
+    if ((rc = phase_rr(ctx, op, (const z_t *)d_Q, ldq, m, s.theta, (z_t *)d_V, (z_t *)d_HV)))
         return rc;
     if (h_resid) {
         ChaseScalars one{};
@@ -672,6 +747,38 @@ int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t l
         CK(cudaMemcpyAsync(h_resid, s.resid, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
     }
     CK(cudaMemcpyAsync(h_theta, s.theta, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    return sync_scalars(ctx);
+}
+
+int chase_gram(bsechase_ctx *ctx, const void *d_A, int64_t lda, const void *d_B, int64_t ldb,
+               int64_t K, int m1, int m2, void *d_G, int64_t ldg) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_A || !d_B || !d_G || K < 1 || lda < K || ldb < K || m1 < 1 || m2 < 1 || m1 > kMaxM ||
+        m2 > kMaxM || ldg < m1)
+        return fail(ctx, BSE_EINVAL, "bad Gram arguments%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    if ((rc = ensure(ctx, ctx->part, (size_t)kCnWork * sizeof(z_t)))) return rc;
+    CK(launch_zgemm_cn(m1, m2, K, (const z_t *)d_A, lda, (const z_t *)d_B, ldb, (z_t *)d_G, ldg,
+                       0.0, 0, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    return BSE_OK;
+}
+
+int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
+               int64_t ldy, int n, void *d_C, int64_t ldc, int precision) {
+    if (!ctx) return BSE_EINVAL;
+    if (!d_H || !d_Y || !d_C || N < 1 || ldh < N || ldy < N || ldc < N || n < 1 || n > kMaxM ||
+        !precision_valid(precision))
+        return fail(ctx, BSE_EINVAL, "bad product arguments%s");
+    DeviceGuard g(ctx->device);
+    int rc;
+    CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
+           precision == CHASE_MIXED_FP32};
+    if ((rc = hop_prepare(ctx, op, n))) return rc;
+    GemmEpi plain{};
+    if ((rc = hop_apply(ctx, op, n, (const z_t *)d_Y, ldy, (z_t *)d_C, ldc, plain))) return rc;
     return sync_scalars(ctx);
 }
 

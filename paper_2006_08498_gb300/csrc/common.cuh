@@ -63,6 +63,7 @@ enum DevError : int {
     DEV_EIG_NOCONV = 2,    // small eigensolver did not converge
     DEV_NONFINITE = 3,     // NaN or Inf met in a reduction
     DEV_BAD_ARG = 4,       // a kernel got an argument outside its limits
+    DEV_TIMEOUT = 5,       // a bounded wait inside a kernel expired
 };
 
 // Scalars shared between the kernels of one solve (device resident).

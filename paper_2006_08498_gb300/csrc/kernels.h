@@ -38,6 +38,27 @@ cudaError_t launch_zgemm_cn(int64_t m1, int64_t m2, int64_t K, const z_t *A, int
                             const z_t *B, int64_t ldb, z_t *G, int64_t ldg, double shift,
                             int hermitize, z_t *work, int64_t work_elems, cudaStream_t st);
 
+// ---- FP64-accurate products on the BF16 tensor cores (ozaki.cu)
+// H sliced once per solve: A slices (ozaki_a_bytes), row exponents E
+// (padded length), and the TMA descriptor of the slices.
+struct OzakiH {
+    int64_t N = 0, Np = 0;
+    void *A = nullptr;
+    int *E = nullptr;
+    alignas(64) unsigned char tmap[128];
+};
+int64_t ozaki_padded(int64_t N);
+size_t ozaki_a_bytes(int64_t N);
+size_t ozaki_b_bytes(int64_t N, int m);
+cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cudaStream_t st);
+// C[N x n] = epi(H Y), Y: N x n (ld ldy); bslices >= ozaki_b_bytes(N, n),
+// F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
+// low = 0: FP64 accuracy (21 slice pairs); low = 1: FP32-level accuracy (the
+// first three slices, 6 pairs, FP32 accumulation).
+cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
+                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
+                        cudaStream_t st);
+
 // ---- vector kernels (vec.cu)
 int vec_partial_blocks(int64_t N);
 // out[j] = sum_i |X[i,j]|^2 (sqrt if take_sqrt) for j < nc; partials in work

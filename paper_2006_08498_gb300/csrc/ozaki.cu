@@ -1,0 +1,524 @@
+// FP64-accurate complex products H * Y on the BF16 tensor cores (tcgen05),
+// by the Ozaki scheme (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 2012):
+// each operand is split into S = 6 slices of BETA = 8 bits with a shared
+// power-of-two scale per row of H and per column of Y, slice products are
+// formed on the tensor cores, and the products are summed back in
+// exact integer arithmetic where it matters.  This is the Chebyshev
+// filter's product (Sec. 3 and the Supplement's "Filter" item: a repeated
+// HEMM), the Rayleigh-Ritz product H Q and the Lanczos products.
+//
+// Representation.  With E_i = the exponent of max_k |H_ik| (|H_ik| <
+// 2^E_i), X_ik = rint(H_ik 2^(48 - E_i)) is an integer with |X| <= 2^48,
+// written in balanced base-256 digits t_1 .. t_6 (|t_1| <= 256, |t_p| <=
+// 128 for p >= 2) so that H_ik ~ 2^E_i sum_p t_p 2^(-8p).  Slice p is stored
+// as the BF16 value t_p 2^(-8p) (exact: at most 9 significant bits).  Y is
+// split the same way per column j (exponent F_j), re and im sharing it.
+//
+// Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).  The
+// leading diagonals p + q = 2, 3, 4 are accumulated in FP32 over K chunks of
+// 64, where every partial sum is an integer multiple of 2^(-8(p+q)) below
+// 2^(24 - 8(p+q)) in magnitude, hence exact; after each chunk they are
+// converted to integers and added into a 64-bit integer per output element.
+// Diagonals 5..7 (weight <= 2^-24 of the leading one) accumulate in FP32
+// over the whole K.  Diagonals > 7 are dropped.  The result is recombined in
+// FP64: C_ij = 2^(E_i + F_j) (S_ij 2^-32 + T_ij).
+//
+// Complex arithmetic as two real MMAs per slice pair into one accumulator
+// of 2w columns [re | im]:  Hr x [Yr | Yi]  +  Hi x [-Yi | Yr].
+//
+// Tiling: CTA = 128 rows x 32 complex columns (MMA M = 128, N = 64), K
+// chunks of 64 (one 128-byte swizzle atom).  Warp 0 issues TMA loads, warp 1
+// issues tcgen05.mma, warps 2..5 drain the exact diagonals each chunk and
+// run the epilogue.  TMEM: 2 x 3 exact accumulators + 1 tail = 448 columns.
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int kBeta = 8;
+constexpr int kS = 6;              // slices per operand (stored)
+constexpr int kBM = 128;           // rows per CTA
+constexpr int kW = 32;             // complex columns per CTA
+constexpr int kN = 2 * kW;         // MMA N
+constexpr int kKC = 64;            // K chunk
+constexpr int kAStages = 2;
+constexpr int kBBufs = 2;
+constexpr int kATile = kBM * kKC * 2;                 // 16 KB (one slice part)
+constexpr int kAStageBytes = 2 * kATile;              // Hr_p and Hi_p
+constexpr int kBPart = kW * kKC * 2;                  // 4 KB
+constexpr int kBSlice = 3 * kBPart;                   // [-Yi | Yr | Yi]
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 512;
+
+// Variants: slice pairs with p + q <= MAXD are formed; diagonals 2..EXT are
+// accumulated exactly (EXT < 2: none).  FP64 accuracy: (7, 4).  Mixed
+// precision: (4, 1), the first three slices only, all in FP32.
+template <int MAXD, int EXT>
+struct OzCfg {
+    static constexpr int kSl = MAXD - 1;                       // slices used per operand
+    static constexpr int kNEx = EXT >= 2 ? EXT - 1 : 0;        // exact accumulators
+    static constexpr int kBBufBytes = kSl * kBSlice;
+    static constexpr int kSmem = kAStages * kAStageBytes + kBBufs * kBBufBytes + 1024;
+    static constexpr uint32_t kTail = 2 * kNEx * kN;           // TMEM column of the tail
+    // A slices of a chunk are consumed in the order EXT..kSl (pairs only in
+    // the FP32 tail), then 1..EXT-1, so the exact accumulators are complete
+    // early in the chunk.
+    __host__ __device__ static constexpr int order(int idx) {
+        return (EXT <= 1) ? idx + 1 : (idx <= kSl - EXT ? idx + EXT : idx - (kSl - EXT) );
+    }
+    static constexpr int kLastExactSlice = EXT - 1;
+};
+using CfgFP64 = OzCfg<7, 4>;
+using CfgMixed = OzCfg<4, 1>;
+static_assert(CfgFP64::order(0) == 4 && CfgFP64::order(2) == 6 && CfgFP64::order(3) == 1 &&
+                  CfgFP64::order(5) == 3,
+              "slice order");
+static_assert(CfgFP64::kSmem <= 232448 && CfgFP64::kTail + kN <= kTmemCols, "resources");
+
+__device__ __forceinline__ void split_digits(double x, int E, int *t) {
+    // X = rint(x 2^(48 - E)), |X| <= 2^48; balanced base-256 digits
+    long long X = __double2ll_rn(ldexp(x, kBeta * kS - E));
+#pragma unroll
+    for (int p = kS - 1; p >= 1; p--) {
+        int d = (int)(X & 0xFF);
+        if (d >= 128) d -= 256;
+        X = (X - d) >> 8;
+        t[p] = d;
+    }
+    t[0] = (int)X;
+}
+
+// BF16 bit pattern of v; v has at most 9 significant bits, so dropping the
+// low 16 bits of its FP32 pattern is exact.
+__device__ __forceinline__ uint16_t bf16_exact(float v) {
+    return (uint16_t)(__float_as_uint(v) >> 16);
+}
+
+__device__ __forceinline__ float slice_value(int t, int p) {
+    return (float)t * __int_as_float((127 - kBeta * (p + 1)) << 23);   // t 2^(-8(p+1))
+}
+
+// ----------------------------------------------------------- exponents
+// E[i] = max over the row (rows_are_cols = 0) or column (1) of the frexp
+// exponent of |re| and |im|; INT_MIN for an all-zero line.
+__global__ void k_row_exponent(int64_t N, const z_t *__restrict__ H, int64_t ldh, int *E,
+                               int cols_per_block) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t k0 = (int64_t)blockIdx.y * cols_per_block;
+    const int64_t k1 = (k0 + cols_per_block < N) ? k0 + cols_per_block : N;
+    double mx = 0.0;
+    for (int64_t k = k0; k < k1; k++) {
+        const z_t h = H[i + k * ldh];
+        mx = fmax(mx, fmax(fabs(h.x), fabs(h.y)));
+    }
+    if (mx > 0.0) {
+        int e;
+        frexp(mx, &e);
+        atomicMax(&E[i], e);
+    }
+}
+
+__global__ void k_col_exponent(int64_t N, int n, const z_t *__restrict__ Y, int64_t ldy, int *F) {
+    const int j = blockIdx.y;
+    if (j >= n) return;
+    double mx = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const z_t y = Y[k + j * ldy];
+        mx = fmax(mx, fmax(fabs(y.x), fabs(y.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) {
+        int e;
+        frexp(mx, &e);
+        atomicMax(&F[j], e);
+    }
+}
+
+__global__ void k_fill_int(int *p, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// ------------------------------------------------------------ slicing
+// A slices of H (K-major): A[((p*2 + ri)*Np + i)*Np + k] = slice p of
+// re/im H_ik.  32 x 32 tiles through shared memory; padded rows and columns
+// (>= N) are written as zeros.
+__global__ void k_slice_h(int64_t N, int64_t Np, const z_t *__restrict__ H, int64_t ldh,
+                          const int *__restrict__ E, uint16_t *A) {
+    __shared__ z_t tile[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + tx, k = k0 + r;       // column k, rows i: coalesced
+        tile[r][tx] = (i < N && k < N) ? H[i + k * ldh] : zmk(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, k = k0 + tx;       // row i, consecutive k
+        const z_t h = tile[tx][r];
+        int e = (i < N) ? E[i] : INT_MIN;
+        if (e == INT_MIN) e = 0;
+        int tr[kS], ti[kS];
+        split_digits(h.x, e, tr);
+        split_digits(h.y, e, ti);
+#pragma unroll
+        for (int p = 0; p < kS; p++) {
+            A[((int64_t)(p * 2 + 0) * Np + i) * Np + k] = bf16_exact(slice_value(tr[p], p));
+            A[((int64_t)(p * 2 + 1) * Np + i) * Np + k] = bf16_exact(slice_value(ti[p], p));
+        }
+    }
+}
+
+// B slices of Y (K-major rows): slice q, rows [0, mp) Yr, [mp, 2mp) Yi,
+// [2mp, 3mp) -Yi; B[((q*3 + part)*mp + j)*Np + k].
+__global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__restrict__ Y,
+                          int64_t ldy, const int *__restrict__ F, uint16_t *B) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (k >= Np) return;
+    z_t y = zmk(0.0, 0.0);
+    int e = 0;
+    if (j < n && k < N) {
+        y = Y[k + j * ldy];
+        e = F[j] == INT_MIN ? 0 : F[j];
+    }
+    int tr[kS], ti[kS];
+    split_digits(y.x, e, tr);
+    split_digits(y.y, e, ti);
+#pragma unroll
+    for (int q = 0; q < kS; q++) {
+        B[((int64_t)(q * 3 + 0) * mp + j) * Np + k] = bf16_exact(slice_value(tr[q], q));
+        B[((int64_t)(q * 3 + 1) * mp + j) * Np + k] = bf16_exact(slice_value(ti[q], q));
+        B[((int64_t)(q * 3 + 2) * mp + j) * Np + k] = bf16_exact(slice_value(-ti[q], q));
+    }
+}
+
+// ---------------------------------------------------------- the GEMM
+struct OzArgs {
+    int64_t M;        // rows of the output (N)
+    int n;            // complex columns of the output
+    int mp;           // padded columns (multiple of kW)
+    int nchunks;      // Np / kKC
+    const int *E;     // row exponents of H (padded to Np)
+    const int *F;     // column exponents of Y
+    GemmEpi ep;
+    const z_t *Y;     // FP64 operand (for the CHEB epilogue)
+    int64_t ldy;
+    z_t *C;
+    int64_t ldc;
+    ChaseScalars *sc;
+};
+
+template <class Cfg, int MAXD, int EXT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              OzArgs args) {
+    constexpr int kSl = Cfg::kSl;
+    constexpr int kBBufBytes = Cfg::kBBufBytes;
+    extern __shared__ uint8_t smraw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = sm;                                        // kAStages x 32 KB
+    uint8_t *sB = sm + kAStages * kAStageBytes;              // kBBufs x 72 KB
+    __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kBBufs], emptyB[kBBufs];
+    __shared__ uint64_t exFull[2], exEmpty[2], tailFull;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int jt = blockIdx.x, it = blockIdx.y;
+    const int j0 = jt * kW;
+    const int64_t i0 = (int64_t)it * kBM;
+    const int nch = args.nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
+        for (int s = 0; s < kBBufs; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
+        for (int s = 0; s < 2; s++) { tc::mbar_init(&exFull[s], 1); tc::mbar_init(&exEmpty[s], 4); }
+        tc::mbar_init(&tailFull, 1);
+        abort_flag = 0;
+        tc::mbar_fence_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_base, kTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t kTail = Cfg::kTail;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            tc::prefetch_tmap(&tmA);
+            tc::prefetch_tmap(&tmB);
+            int use = 0;
+            for (int c = 0; c < nch && !abort_flag; c++) {
+                const int bb = c & 1;
+                if (c >= 2 && !tc::mbar_wait(&emptyB[bb], ((c >> 1) - 1) & 1, &abort_flag)) break;
+                tc::mbar_expect_tx(&fullB[bb], kBBufBytes);
+                uint8_t *bdst = sB + bb * kBBufBytes;
+                for (int q = 0; q < kSl; q++) {
+                    const int rb = q * 3 * args.mp;
+                    tc::tma_load_2d(bdst + q * kBSlice + 0 * kBPart, &tmB, c * kKC, rb + 2 * args.mp + j0, &fullB[bb]);
+                    tc::tma_load_2d(bdst + q * kBSlice + 1 * kBPart, &tmB, c * kKC, rb + j0, &fullB[bb]);
+                    tc::tma_load_2d(bdst + q * kBSlice + 2 * kBPart, &tmB, c * kKC, rb + args.mp + j0, &fullB[bb]);
+                }
+                bool ok = true;
+                for (int idx = 0; idx < kSl; idx++, use++) {
+                    const int p = Cfg::order(idx) - 1;
+                    const int st = use % kAStages, n = use / kAStages;
+                    if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                    tc::mbar_expect_tx(&fullA[st], kAStageBytes);
+                    uint8_t *adst = sA + st * kAStageBytes;
+                    const int64_t Np = (int64_t)nch * kKC;
+                    tc::tma_load_2d(adst, &tmA, c * kKC, (int)((p * 2 + 0) * Np + i0), &fullA[st]);
+                    tc::tma_load_2d(adst + kATile, &tmA, c * kKC, (int)((p * 2 + 1) * Np + i0), &fullA[st]);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
+            bool tail_started = false;
+            int use = 0;
+            for (int c = 0; c < nch && !abort_flag; c++) {
+                const int bb = c & 1, ex = c & 1;
+                if (!tc::mbar_wait(&fullB[bb], (c >> 1) & 1, &abort_flag)) break;
+                if (Cfg::kNEx > 0 && c >= 2 &&
+                    !tc::mbar_wait(&exEmpty[ex], ((c >> 1) - 1) & 1, &abort_flag))
+                    break;
+                bool ex_started[3] = {false, false, false};
+                const uint8_t *bsrc = sB + bb * kBBufBytes;
+                bool ok = true;
+                for (int idx = 0; idx < kSl; idx++, use++) {
+                    const int p = Cfg::order(idx);
+                    const int st = use % kAStages, n = use / kAStages;
+                    if (!tc::mbar_wait(&fullA[st], n & 1, &abort_flag)) { ok = false; break; }
+                    tc::fence_after();
+                    const uint8_t *aR = sA + st * kAStageBytes, *aI = aR + kATile;
+                    for (int q = 1; p + q <= MAXD; q++) {
+                        const int g = p + q;
+                        uint32_t d;
+                        bool acc0;
+                        if (g <= EXT) {
+                            d = tmem + (uint32_t)((ex * Cfg::kNEx + (g - 2)) * kN);
+                            acc0 = ex_started[g - 2];
+                            ex_started[g - 2] = true;
+                        } else {
+                            d = tmem + kTail;
+                            acc0 = tail_started;
+                            tail_started = true;
+                        }
+                        const uint8_t *bq = bsrc + (q - 1) * kBSlice;
+                        const uint64_t b_pos = tc::sdesc_sw128(bq + kBPart);   // [Yr | Yi]
+                        const uint64_t b_neg = tc::sdesc_sw128(bq);            // [-Yi | Yr]
+                        const uint64_t a_r = tc::sdesc_sw128(aR), a_i = tc::sdesc_sw128(aI);
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; kk++) {
+                            tc::mma_bf16(d, a_r + 2 * kk, b_pos + 2 * kk, idesc, (acc0 || kk > 0) ? 1u : 0u);
+                            tc::mma_bf16(d, a_i + 2 * kk, b_neg + 2 * kk, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&emptyA[st]);
+                    if (Cfg::kNEx > 0 && p == Cfg::kLastExactSlice) tc::mma_commit(&exFull[ex]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&emptyB[bb]);
+            }
+            tc::mma_commit(&tailFull);
+        }
+    } else {
+        // ------------------------------------------------ drain + epilogue
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        long long S[kN];
+#pragma unroll
+        for (int j = 0; j < kN; j++) S[j] = 0;
+        bool ok = true;
+        for (int c = 0; Cfg::kNEx > 0 && c < nch; c++) {
+            const int ex = c & 1;
+            if (!tc::mbar_wait(&exFull[ex], (c >> 1) & 1, &abort_flag)) { ok = false; break; }
+            tc::fence_after();
+#pragma unroll
+            for (int g = 2; g <= EXT; g++) {
+                const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
+                const int shift = kBeta * (4 - g);                             // S in units of 2^-32
+#pragma unroll
+                for (int h = 0; h < kN / 16; h++) {
+                    uint32_t r[16];
+                    tc::tmem_ld16(tmem + lane_addr + (uint32_t)((ex * Cfg::kNEx + (g - 2)) * kN + h * 16), r);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const int d = __float2int_rn(__uint_as_float(r[u]) * scale);
+                        S[h * 16 + u] += (long long)d << shift;
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&exEmpty[ex]);
+        }
+        if (ok && tc::mbar_wait(&tailFull, 0, &abort_flag)) {
+            tc::fence_after();
+            const int64_t i = i0 + row;
+            int e = (i < args.M) ? args.E[i] : 0;
+            if (e == INT_MIN) e = 0;
+#pragma unroll
+            for (int h = 0; h < kW / 16; h++) {
+                uint32_t rr[16], ri[16];
+                tc::tmem_ld16(tmem + lane_addr + kTail + h * 16, rr);
+                tc::tmem_ld16(tmem + lane_addr + kTail + kW + h * 16, ri);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 16; u++) {
+                    const int jl = h * 16 + u, j = j0 + jl;
+                    if (i >= args.M || j >= args.n) continue;
+                    int f = args.F[j];
+                    if (f == INT_MIN) f = 0;
+                    const double cr = ldexp((double)S[jl] * 0x1.0p-32 + (double)__uint_as_float(rr[u]), e + f);
+                    const double ci = ldexp((double)S[kW + jl] * 0x1.0p-32 + (double)__uint_as_float(ri[u]), e + f);
+                    z_t v = zmk(cr, ci);
+                    if (args.ep.mode == GEMM_CHEB) {
+                        const z_t y = args.Y[i + j * args.ldy];
+                        v = zscale(zsub(v, zscale(y, args.ep.c)), args.ep.s1);
+                        if (args.ep.Yp) v = zsub(v, zscale(args.ep.Yp[i + j * args.ep.ldyp], args.ep.s2));
+                    }
+                    args.C[i + j * args.ldc] = v;
+                }
+            }
+        }
+        (void)ok;
+    }
+
+    tc::fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.y * gridDim.x + blockIdx.x);
+    if (warp == 1) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor [rows][K] (K contiguous), box of 64 x box_rows, 128-byte swizzle
+bool make_map(CUtensorMap *m, void *base, uint64_t K, uint64_t rows, uint32_t box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {K, rows};
+    cuuint64_t strides[1] = {K * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int64_t ozaki_padded(int64_t N) { return (N + 127) / 128 * 128; }
+
+size_t ozaki_a_bytes(int64_t N) {
+    const int64_t Np = ozaki_padded(N);
+    return (size_t)kS * 2 * Np * Np * 2;
+}
+
+size_t ozaki_b_bytes(int64_t N, int m) {
+    const int64_t Np = ozaki_padded(N);
+    const int mp = (m + kW - 1) / kW * kW;
+    return (size_t)kS * 3 * mp * Np * 2;
+}
+
+cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cudaStream_t st) {
+    const int64_t Np = ozaki_padded(N);
+    oh->N = N;
+    oh->Np = Np;
+    k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
+    bse_count_launches(1);
+    const int cpb = 256;
+    dim3 g1((unsigned)((N + 255) / 256), (unsigned)((N + cpb - 1) / cpb));
+    k_row_exponent<<<g1, 256, 0, st>>>(N, H, ldh, oh->E, cpb);
+    bse_count_launches(1);
+    dim3 g2((unsigned)(Np / 32), (unsigned)(Np / 32));
+    k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
+    bse_count_launches(1);
+    if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * Np), kBM))
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <class Cfg, int MAXD, int EXT>
+cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a,
+                           dim3 grid, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_ozaki_zgemm<Cfg, MAXD, EXT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_ozaki_zgemm<Cfg, MAXD, EXT><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
+    bse_count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
+                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
+                        cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t N = oh.N, Np = oh.Np;
+    const int mp = (n + kW - 1) / kW * kW;
+    k_fill_int<<<(mp + 255) / 256, 256, 0, st>>>(F, mp, INT_MIN);
+    bse_count_launches(1);
+    dim3 ge((unsigned)std::min<int64_t>((N + 255) / 256, 16), (unsigned)n);
+    k_col_exponent<<<ge, 256, 0, st>>>(N, n, Y, ldy, F);
+    bse_count_launches(1);
+    dim3 gs((unsigned)((Np + 255) / 256), (unsigned)mp);
+    k_slice_y<<<gs, 256, 0, st>>>(N, Np, n, mp, Y, ldy, F, (uint16_t *)bslices);
+    bse_count_launches(1);
+    CUtensorMap tmB;
+    if (!make_map(&tmB, bslices, (uint64_t)Np, (uint64_t)(kS * 3 * mp), kW))
+        return cudaErrorInvalidValue;
+    OzArgs a;
+    a.M = N;
+    a.n = n;
+    a.mp = mp;
+    a.nchunks = (int)(Np / kKC);
+    a.E = oh.E;
+    a.F = F;
+    a.ep = ep;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.C = C;
+    a.ldc = ldc;
+    a.sc = sc;
+    dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM));
+    const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
+    if (low) return launch_variant<CfgMixed, 4, 1>(tmA, tmB, a, grid, st);
+    return launch_variant<CfgFP64, 7, 4>(tmA, tmB, a, grid, st);
+}

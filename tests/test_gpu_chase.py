@@ -99,21 +99,85 @@ def test_generator_full_size_sampled(ctx):
     torch.cuda.empty_cache()
 
 
+# ----------------------------------------------- the filter's product H Y
+
+# Normwise bound per column: ||C_j - (HY)_j|| <= tol ||H||_2 ||Y_j||.  The
+# tensor-core emulation keeps 48 bits of each operand relative to its row
+# (column) maximum, sums the leading slice products exactly and the tail in
+# FP32: tol = 1e-12.  Native FP64 GEMM: tol = 1e-14.
+EMUL_TOL, DFMA_TOL = 1e-12, 1e-14
+
+
+def colwise_err(C, A, Y):
+    nA = np.linalg.norm(A, 2)
+    return np.linalg.norm(C - A @ Y, axis=0) / (nA * np.maximum(np.linalg.norm(Y, axis=0), 1e-300))
+
+
+@pytest.mark.parametrize("n,m,seed", [(333, 7, 1), (1000, 40, 2), (129, 33, 3), (64, 1, 4)])
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_FP64_DFMA])
+def test_hemm_matches_fp64(ctx, n, m, seed, precision):
+    A, _ = hermitian(n, seed)
+    Y = block(n, m, seed + 1)
+    Y[:, 0] *= 1e-9                      # columns of very different scale
+    if m > 2:
+        Y[:, 2] *= 3e7
+        Y[5, 1] = 1e5                    # one dominant entry in a column
+    C = host(ctx.hemm(dev(A), dev(Y), precision=precision))
+    tol = EMUL_TOL if precision == pkg.CHASE_FP64 else DFMA_TOL
+    assert np.max(colwise_err(C, A, Y)) <= tol
+
+
+def test_hemm_fp32_level(ctx):
+    """The mixed-precision product: the first three 8-bit slices, FP32
+    accumulation: FP32-level accuracy."""
+    A, _ = hermitian(700, 5)
+    Y = block(700, 50, 6)
+    C = host(ctx.hemm(dev(A), dev(Y), precision=pkg.CHASE_MIXED_FP32))
+    err = colwise_err(C, A, Y)
+    assert np.max(err) <= 2e-6
+    assert np.max(err) >= 1e-12          # it is not the FP64-accurate product
+
+
+def test_hemm_zero_column_and_bse_matrix(ctx):
+    H = oracle.build_h(0, 125, 4, 4)
+    Y = block(2000, 75, 9)
+    Y[:, 10] = 0
+    C = host(ctx.hemm(dev(H), dev(Y)))
+    assert np.all(C[:, 10] == 0)
+    err = colwise_err(C, H, Y)
+    err[10] = 0.0
+    assert np.max(err) <= EMUL_TOL
+
+
+@pytest.mark.parametrize("K,m1,m2", [(20000, 140, 140), (333, 7, 40), (100000, 3, 1)])
+def test_gram_matches_fp64(ctx, K, m1, m2):
+    A = block(K, m1, 11)
+    B = block(K, m2, 12)
+    G = host(ctx.gram(dev(A), dev(B)))
+    ref = A.conj().T @ B
+    bound = np.abs(A).T @ np.abs(B)
+    assert np.all(np.abs(G - ref) <= 1e-12 * bound)
+    assert np.array_equal(G, host(ctx.gram(dev(A), dev(B))))     # deterministic
+
+
 # -------------------------------------------------------------- Lanczos
 
-def test_lanczos_matches_oracle(ctx):
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_FP64_DFMA])
+def test_lanczos_matches_oracle(ctx, precision):
     H = oracle.build_h(0, 125, 4, 4)
     est_o = oracle.lanczos_bounds(H, 75, seed=3)
-    est_g = ctx.lanczos(dev(H), 75, steps=25, runs=4, seed=3)
+    est_g = ctx.lanczos(dev(H), 75, steps=25, runs=4, seed=3, precision=precision)
+    tight = precision == pkg.CHASE_FP64_DFMA
     for key in ("beta", "mu_1", "norm_est"):
-        assert est_g[key] == pytest.approx(est_o[key], rel=1e-11)
-    assert est_g["mu_m"] == pytest.approx(est_o["mu_m"], rel=1e-8)
+        assert est_g[key] == pytest.approx(est_o[key], rel=1e-11 if tight else 1e-9)
+    assert est_g["mu_m"] == pytest.approx(est_o["mu_m"], rel=1e-8 if tight else 1e-6)
 
 
 # --------------------------------------------------------------- filter
 
 @pytest.mark.parametrize("n,m,seed", [(333, 7, 1), (257, 40, 2), (2000, 75, 3)])
-def test_filter_matches_oracle(ctx, n, m, seed):
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_FP64_DFMA])
+def test_filter_matches_oracle(ctx, n, m, seed, precision):
     if n == 2000:
         A = oracle.build_h(0, 125, 4, 4)
         lam = np.linalg.eigvalsh(A)
@@ -125,11 +189,12 @@ def test_filter_matches_oracle(ctx, n, m, seed):
     c, e = oracle.filter_interval(lam[min(m, n - 1)], lam[-1] + 0.05)
     Yo, mv_o = oracle.chebyshev_filter(A, V, deg, lower, c, e)
     Vd = dev(V)
-    mv = ctx.filter(dev(A), Vd, deg, lower, c, e)
+    mv = ctx.filter(dev(A), Vd, deg, lower, c, e, precision=precision)
     Yg = host(Vd)
     assert mv == mv_o == int(np.sum(deg))
     err = np.linalg.norm(Yg - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
-    assert np.max(err) <= 1e-11
+    # per step the emulated product is within ~2^-38 of |H||Y| (vs ~1e-16)
+    assert np.max(err) <= (1e-9 if precision == pkg.CHASE_FP64 else 1e-11)
 
 
 def test_filter_single_degree_closed_form(ctx):
@@ -174,11 +239,12 @@ def test_qr_matches_oracle(ctx, n, k, m):
 
 # ---------------------------------------------------------- Rayleigh-Ritz
 
-def test_rayleigh_ritz_matches_oracle(ctx):
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_FP64_DFMA])
+def test_rayleigh_ritz_matches_oracle(ctx, precision):
     A, lam = hermitian(500, 8)
     Q = orthonormal(500, 30, 9)
     th_o, V_o, HV_o = oracle.rayleigh_ritz(A, Q)
-    th_g, Vd, HVd, res = ctx.rayleigh_ritz(dev(A), dev(Q), norm=2.0)
+    th_g, Vd, HVd, res = ctx.rayleigh_ritz(dev(A), dev(Q), norm=2.0, precision=precision)
     V_g, HV_g = host(Vd), host(HVd)
     assert np.allclose(th_g, th_o, rtol=1e-12, atol=1e-13)
     assert np.allclose(res, oracle.residuals(HV_o, V_o, th_o, 2.0), rtol=1e-8, atol=1e-14)
@@ -217,18 +283,35 @@ def c1():
     return H, w, ref
 
 
-def test_solve_c1_matches_oracle(ctx, c1):
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_FP64_DFMA])
+def test_solve_c1_matches_oracle(ctx, c1, precision):
     """N = 2000, nev = 50, nex = 25, tol 1e-10: against the dense oracle and
     the oracle's own ChASE run with the same seeds."""
     H, w, ref = c1
     Hd = ctx.build_hamiltonian(0, 125, 4, 4)
-    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, precision=precision)
     V = host(Vd)
     _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
     assert np.max(resid) <= 1e-10
     assert np.allclose(evals, ref["evals"], rtol=1e-12, atol=0)
     assert abs(st["iters"] - ref["iters"]) <= 1
     assert st["iters"] >= 2
+
+
+def test_solve_mixed_precision(ctx, c1):
+    """Mixed precision: FP32-level filter sweeps, then FP64-accurate closing
+    sweeps.  Same tolerances as the FP64 path, and per-pair agreement with
+    the FP64 solve."""
+    H, w, ref = c1
+    Hd = ctx.build_hamiltonian(0, 125, 4, 4)
+    e64, V64, r64, s64 = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, precision=pkg.CHASE_FP64)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36,
+                                     precision=pkg.CHASE_MIXED_FP32)
+    V = host(Vd)
+    _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
+    assert np.max(resid) <= 1e-10
+    assert 0 < st["filter_matvecs_low"] < st["filter_matvecs"]
+    assert np.max(np.abs(evals - e64) / np.abs(e64)) <= 1e-12
 
 
 def test_solve_is_deterministic(ctx):
