@@ -195,6 +195,22 @@ int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t l
 int chase_gram(bsechase_ctx *ctx, const void *d_A, int64_t lda, const void *d_B, int64_t ldb,
                int64_t K, int m1, int m2, void *d_G, int64_t ldg);
 
+/* Allocation-free Gram product, for callers that cannot allocate device
+ * memory (their memory manager owns the device, they cannot afford the
+ * allocator's synchronisation, or they cannot create a context, which
+ * allocates workspace).  The paper has no counterpart: it is a service entry
+ * point.  Same result as chase_gram (G = A^H B, m1 x m2, ldg >= m1, for A: K x
+ * m1, B: K x m2) computed on the current device and on `cuda_stream` (NULL =
+ * the default stream); the call returns once the work is enqueued.  The
+ * split-K partial sums live in a fixed 4 MiB device array inside the library
+ * (held by every GPU that loads it, until exit), so no memory is allocated;
+ * m1, m2 > 512 is rejected with BSE_EINVAL.  The first call on a device looks
+ * up that array's address; make it before any stream capture begins.  Every
+ * call shares the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  Errors: BSE_EINVAL, BSE_ECUDA. */
+int chase_gram_noalloc(const void *d_A, int64_t lda, const void *d_B, int64_t ldb, int64_t K,
+                       int m1, int m2, void *d_G, int64_t ldg, void *cuda_stream);
+
 /* The filter's matrix product alone: d_C = H d_Y (d_Y: N x n, ldy; d_C: N x n,
  * ldc; 1 <= n <= 512) at the given precision (Sec. 3: the filter is a
  * repeated HEMM).  d_C must not overlap d_H or d_Y. */

@@ -26,7 +26,7 @@ ABI_SYMBOLS = (
     "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
-    "chase_gram",
+    "chase_gram", "chase_gram_noalloc",
 )
 
 
@@ -115,6 +115,8 @@ def load():
     L.chase_hemm.restype = i32
     L.chase_gram.argtypes = [P, P, i64, P, i64, i64, i32, i32, P, i64]
     L.chase_gram.restype = i32
+    L.chase_gram_noalloc.argtypes = [P, i64, P, i64, i64, i32, i32, P, i64, P]
+    L.chase_gram_noalloc.restype = i32
     _lib = L
     return L
 
@@ -144,6 +146,22 @@ def _ld(t):
     if not t.flags["F_CONTIGUOUS"]:
         raise ValueError("array must be Fortran-ordered")
     return t.shape[0]
+
+
+def gram_noalloc(A, B, out, stream=None):
+    """G = A^H B through the allocation-free entry point chase_gram_noalloc:
+    the caller provides the output `out` (m1 x m2, column-major, on A's
+    device); the library allocates nothing.  Runs on `stream` (a
+    torch.cuda.Stream; default: the current stream) and returns the status."""
+    import torch
+    K, m1 = A.shape
+    m2 = B.shape[1]
+    if stream is None:
+        stream = torch.cuda.current_stream(A.device)
+    return load().chase_gram_noalloc(ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                     ctypes.c_void_p(B.data_ptr()), _ld(B), K, m1, m2,
+                                     ctypes.c_void_p(out.data_ptr()), _ld(out),
+                                     ctypes.c_void_p(stream.cuda_stream))
 
 
 def colmajor_empty(rows, cols, device="cuda", dtype=None):
