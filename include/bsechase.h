@@ -55,12 +55,14 @@ typedef enum {
                              Rayleigh-Ritz) run on the BF16 tensor cores as an
                              Ozaki-scheme emulation: 6 slices of 8 bits per
                              operand, exact integer accumulation of the
-                             leading slice products, FP32 for the rest (error
-                             ~1e-12 relative to |H||Y|).  QR, reduced eig,
+                             slice diagonals 2..5 per K chunk of 64, FP32 for
+                             diagonals 6..7 (normwise error ~1e-12 relative
+                             to ||H|| ||Y||).  QR, reduced eig,
                              residuals and locking in native FP64.          */
     CHASE_MIXED_FP32 = 1, /* filter products at FP32-level accuracy on the
-                             tensor cores (first 3 slices, FP32 accumulation)
-                             while every unlocked residual exceeds 1e-6, then
+                             tensor cores (first 4 slices: 32 bits relative to
+                             the row/column maximum, 10 slice pairs) while
+                             every unlocked residual exceeds 1e-6, then
                              FP64-accurate filter sweeps; Lanczos, QR,
                              Rayleigh-Ritz and residuals as in CHASE_FP64.
                              In single-phase entry points it selects the
@@ -216,6 +218,60 @@ int chase_gram_noalloc(const void *d_A, int64_t lda, const void *d_B, int64_t ld
  * repeated HEMM).  d_C must not overlap d_H or d_Y. */
 int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
                int64_t ldy, int n, void *d_C, int64_t ldc, int precision);
+
+/* ---- request server (continuous batching of many solves on one GPU) ------
+ * The paper's BSE workflow solves sequences of related eigenproblems (k-mesh
+ * and energy-cutoff convergence tests, Sec. 2 and Sec. 4); the server runs a
+ * stream of such solves.  Requests are admitted in FIFO order when a slot is
+ * free and their memory estimate fits the HBM budget; each slot has its own
+ * stream, so admitted requests run concurrently; results (eigenvalues,
+ * residuals, stats, latency stamps) stay with the server until released, and
+ * eigenvectors stay on the device (LRU-evicted under the budget) so later
+ * requests can warm-start from them. */
+
+typedef struct {
+    uint64_t seed;           /* synthetic Hamiltonian: bse_build_hamiltonian   */
+    int Nk, Nv, Nc;
+    int use_model;           /* 0: default model parameters                    */
+    bse_model model;
+    int nev, nex;            /* as chase_solve                                 */
+    double tol;
+    int deg_max, precision;
+    uint64_t warm_ticket;    /* 0, or a ticket whose eigenvectors (same N) start
+                                this solve if that request has finished       */
+} chase_request;
+
+typedef struct {
+    int status;              /* the solve's status (as chase_solve)           */
+    int has_evecs;           /* eigenvectors resident (chase_server_evecs)     */
+    int64_t N;
+    int nev;
+    const double *evals;     /* nev, ascending; valid until released          */
+    const double *resid;     /* nev                                          */
+    chase_stats stats;
+    double t_submit, t_start, t_end;  /* seconds, steady clock                */
+} chase_result;
+
+/* Start a server on ctx's device: max_slots (1..64) concurrent solves within
+ * hbm_budget_bytes of admitted memory.  One server per context. */
+int chase_server_create(bsechase_ctx *ctx, size_t hbm_budget_bytes, int max_slots);
+/* Queue a request; *ticket identifies it.  BSE_EINVAL (bad request), BSE_ENOMEM
+ * (its estimate exceeds the whole budget). */
+int chase_server_submit(bsechase_ctx *ctx, const chase_request *req, uint64_t *ticket);
+/* BSE_EBUSY while pending; BSE_OK and *out filled when finished. */
+int chase_server_poll(bsechase_ctx *ctx, uint64_t ticket, chase_result *out);
+/* Block up to timeout_s seconds; BSE_ETIMEOUT if still pending. */
+int chase_server_wait(bsechase_ctx *ctx, uint64_t ticket, double timeout_s, chase_result *out);
+/* Copy a finished request's eigenvectors (N x nev) to d_out (device or host
+ * memory, leading dimension ld >= N). */
+int chase_server_evecs(bsechase_ctx *ctx, uint64_t ticket, void *d_out, int64_t ld);
+/* Cancel a queued request, or drop a finished one's results and eigenvectors
+ * (BSE_EBUSY while it runs or while a queued warm start depends on it). */
+int chase_server_release(bsechase_ctx *ctx, uint64_t ticket);
+/* Admitted bytes (running + resident), queued and running requests. */
+int chase_server_info(bsechase_ctx *ctx, size_t *held_bytes, int *queued, int *running);
+/* Stop the workers (waits for running solves) and free everything. */
+int chase_server_destroy(bsechase_ctx *ctx);
 
 #ifdef __cplusplus
 }

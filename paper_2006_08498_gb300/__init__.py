@@ -27,6 +27,8 @@ ABI_SYMBOLS = (
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
     "chase_gram", "chase_gram_noalloc",
+    "chase_server_create", "chase_server_submit", "chase_server_poll", "chase_server_wait",
+    "chase_server_evecs", "chase_server_release", "chase_server_info", "chase_server_destroy",
 )
 
 
@@ -62,6 +64,31 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("Nk", ctypes.c_int), ("Nv", ctypes.c_int),
+                ("Nc", ctypes.c_int), ("use_model", ctypes.c_int), ("model", Model),
+                ("nev", ctypes.c_int), ("nex", ctypes.c_int), ("tol", ctypes.c_double),
+                ("deg_max", ctypes.c_int), ("precision", ctypes.c_int),
+                ("warm_ticket", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("has_evecs", ctypes.c_int), ("N", ctypes.c_int64),
+                ("nev", ctypes.c_int), ("evals", ctypes.POINTER(ctypes.c_double)),
+                ("resid", ctypes.POINTER(ctypes.c_double)), ("stats", Stats),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_end", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.nev
+        return dict(status=self.status, N=self.N, nev=n, has_evecs=bool(self.has_evecs),
+                    evals=np.array(self.evals[:n]) if self.evals else None,
+                    resid=np.array(self.resid[:n]) if self.resid else None,
+                    stats=self.stats.as_dict(), t_submit=self.t_submit,
+                    t_start=self.t_start, t_end=self.t_end,
+                    latency=self.t_end - self.t_submit)
 
 
 DEFAULT_MODEL = dict(band_gap=2.0, w0=0.3, x0=0.5, jitter=0.01, dispersion=1.0, rank_x=8)
@@ -117,6 +144,18 @@ def load():
     L.chase_gram.restype = i32
     L.chase_gram_noalloc.argtypes = [P, i64, P, i64, i64, i32, i32, P, i64, P]
     L.chase_gram_noalloc.restype = i32
+    sz = ctypes.c_size_t
+    L.chase_server_create.argtypes = [P, sz, i32]
+    L.chase_server_submit.argtypes = [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.chase_server_poll.argtypes = [P, u64, ctypes.POINTER(Result)]
+    L.chase_server_wait.argtypes = [P, u64, dbl, ctypes.POINTER(Result)]
+    L.chase_server_evecs.argtypes = [P, u64, P, i64]
+    L.chase_server_release.argtypes = [P, u64]
+    L.chase_server_info.argtypes = [P, ctypes.POINTER(sz), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32)]
+    L.chase_server_destroy.argtypes = [P]
+    for f in ("create", "submit", "poll", "wait", "evecs", "release", "info", "destroy"):
+        getattr(L, "chase_server_" + f).restype = i32
     _lib = L
     return L
 
@@ -331,6 +370,58 @@ class Context:
                                ctypes.c_void_p(G.data_ptr()), _ld(G))
         self._check(rc)
         return G
+
+    # ------------------------------------------------------------ serving
+    def server_create(self, hbm_budget_bytes, max_slots):
+        self._check(load().chase_server_create(self._h, int(hbm_budget_bytes), max_slots))
+
+    def server_destroy(self):
+        self._check(load().chase_server_destroy(self._h))
+
+    def submit(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
+               model=None, warm_ticket=0):
+        """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc);
+        returns its ticket."""
+        md = dict(DEFAULT_MODEL)
+        if model:
+            md.update(model)
+        r = Request(seed, Nk, Nv, Nc, 1 if model else 0,
+                    Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
+                          int(md["rank_x"])),
+                    nev, nex, tol, deg_max, precision, warm_ticket)
+        t = ctypes.c_uint64(0)
+        self._check(load().chase_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """Result dict, or None while pending."""
+        out = Result()
+        rc = load().chase_server_poll(self._h, ticket, ctypes.byref(out))
+        if rc == BSE_EBUSY:
+            return None
+        self._check(rc)
+        return out.as_dict()
+
+    def wait(self, ticket, timeout_s=600.0):
+        """Result dict; raises BseError(BSE_ETIMEOUT) if still pending."""
+        out = Result()
+        self._check(load().chase_server_wait(self._h, ticket, timeout_s, ctypes.byref(out)))
+        return out.as_dict()
+
+    def fetch_evecs(self, ticket, N, nev):
+        V = colmajor_empty(N, nev, device="cuda:%d" % self.device)
+        self._check(load().chase_server_evecs(self._h, ticket, ctypes.c_void_p(V.data_ptr()),
+                                              _ld(V)))
+        return V
+
+    def release(self, ticket):
+        return load().chase_server_release(self._h, ticket)
+
+    def server_info(self):
+        held, q, r = ctypes.c_size_t(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(load().chase_server_info(self._h, ctypes.byref(held), ctypes.byref(q),
+                                             ctypes.byref(r)))
+        return dict(held_bytes=held.value, queued=q.value, running=r.value)
 
     def rayleigh_ritz(self, H, Q, norm=1.0, precision=CHASE_FP64):
         N, m = Q.shape

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/bsechase.h"
+#include "context.h"
 #include "kernels.h"
 
 namespace {
@@ -29,33 +30,9 @@ constexpr double kKappaMax = 1e12;             // cap on the filter's amplificat
 constexpr double kMixedSwitch = 1e-6;
 constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
 }  // namespace
 
-struct bsechase_ctx {
-    int device = 0;
-    cudaStream_t st = nullptr;
-    bool own_stream = false;
-    std::string err;
-    ChaseScalars *sc = nullptr;      // device
-    ChaseScalars *hsc = nullptr;     // pinned host mirror
-    // workspace
-    DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
-    DevBuf ozA, ozE, ozB, ozF;       // tensor-core products: slices of H and of the operand
-    OzakiH oh;
-    int64_t wsN = 0;
-    int wsM = 0;
-    cudaEvent_t ev[8];
-    bool ev_ok = false;
-};
-
-namespace {
-
-int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail = "") {
+int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, detail);
     c->err = buf;
@@ -68,13 +45,16 @@ int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail = "") {
         if (e_ != cudaSuccess) return fail(ctx, BSE_ECUDA, "CUDA error: %s", cudaGetErrorString(e_)); \
     } while (0)
 
+// Grow a workspace buffer; allocations are stream-ordered on the context's
+// stream, so growing one context's workspace never synchronises the device
+// (other contexts keep running).
 int ensure(bsechase_ctx *ctx, DevBuf &b, size_t bytes) {
     if (b.bytes >= bytes) return BSE_OK;
-    if (b.p) cudaFree(b.p);
+    if (b.p) cudaFreeAsync(b.p, ctx->st);
     b.p = nullptr;
     b.bytes = 0;
     if (bytes == 0) return BSE_OK;
-    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&b.p, bytes, ctx->st) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, BSE_ENOMEM, "cannot allocate %s of device workspace",
                     std::to_string(bytes).c_str());
@@ -82,6 +62,22 @@ int ensure(bsechase_ctx *ctx, DevBuf &b, size_t bytes) {
     b.bytes = bytes;
     return BSE_OK;
 }
+
+void release_workspace(bsechase_ctx *ctx) {
+    DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
+                      &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
+                      &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
+                      &ctx->ozB, &ctx->ozF};
+    for (DevBuf *b : bufs) {
+        if (b->p) cudaFreeAsync(b->p, ctx->st);
+        b->p = nullptr;
+        b->bytes = 0;
+    }
+    ctx->wsN = 0;
+    ctx->wsM = 0;
+}
+
+namespace {
 
 // Small-array layout inside small_d (doubles) and ints.
 struct Small {
@@ -180,7 +176,7 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     if ((rc = ensure(ctx, ctx->ozF, (size_t)(mc + 64) * sizeof(int)))) return rc;
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
-    CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->st));
+    CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
     return BSE_OK;
 }
 
@@ -359,6 +355,8 @@ int validate_solve(bsechase_ctx *ctx, const void *H, int64_t N, int64_t ldh, int
     return BSE_OK;
 }
 
+}  // namespace
+
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
                  z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats) {
@@ -512,6 +510,8 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     return BSE_OK;
 }
 
+namespace {
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int d) {
@@ -580,13 +580,11 @@ int bsechase_create(bsechase_ctx **out, int device, void *stream) {
 void bsechase_destroy(bsechase_ctx *ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
-    if (ctx->st) cudaStreamSynchronize(ctx->st);
-    DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
-                      &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
-                      &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
-                      &ctx->ozB, &ctx->ozF};
-    for (DevBuf *b : bufs)
-        if (b->p) cudaFree(b->p);
+    bse_server_shutdown(ctx);
+    if (ctx->st) {
+        release_workspace(ctx);
+        cudaStreamSynchronize(ctx->st);
+    }
     if (ctx->sc) cudaFree(ctx->sc);
     if (ctx->hsc) cudaFreeHost(ctx->hsc);
     for (int i = 0; i < 8; i++)

@@ -1,0 +1,46 @@
+// The solver context shared by the host-side files of the library
+// (chase.cu: solver and C ABI; serve.cu: request server).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/bsechase.h"
+#include "kernels.h"
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct BseServer;
+
+struct bsechase_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    ChaseScalars *sc = nullptr;      // device
+    ChaseScalars *hsc = nullptr;     // pinned host mirror
+    // workspace
+    DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
+    DevBuf ozA, ozE, ozB, ozF;       // tensor-core products: slices of H and of the operand
+    OzakiH oh;
+    int64_t wsN = 0;
+    int wsM = 0;
+    cudaEvent_t ev[8];
+    bool ev_ok = false;
+    BseServer *server = nullptr;     // request server attached to this context
+};
+
+// Record a failure message (printf-style with one string argument).
+int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail = "");
+// Grow / free the context's workspace (stream-ordered on ctx->st).
+int ensure(bsechase_ctx *ctx, DevBuf &b, size_t bytes);
+void release_workspace(bsechase_ctx *ctx);
+// The whole solve on device buffers (chase_solve without argument checks).
+int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
+                 double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
+                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
+// Stop and free the request server of a context (no-op without one).
+void bse_server_shutdown(bsechase_ctx *ctx);

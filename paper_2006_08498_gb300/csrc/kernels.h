@@ -50,11 +50,13 @@ struct OzakiH {
 int64_t ozaki_padded(int64_t N);
 size_t ozaki_a_bytes(int64_t N);
 size_t ozaki_b_bytes(int64_t N, int m);
-cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cudaStream_t st);
+// Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
+cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
+                            cudaStream_t st);
 // C[N x n] = epi(H Y), Y: N x n (ld ldy); bslices >= ozaki_b_bytes(N, n),
 // F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
-// low = 0: FP64 accuracy (21 slice pairs); low = 1: FP32-level accuracy (the
-// first three slices, 6 pairs, FP32 accumulation).
+// low = 0: FP64 accuracy (6 slices, 21 slice pairs); low = 1: FP32-level
+// accuracy (the first four slices, 10 pairs, all exact).
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
                         cudaStream_t st);

@@ -14,22 +14,28 @@
 // as the BF16 value t_p 2^(-8p) (exact: at most 9 significant bits).  Y is
 // split the same way per column j (exponent F_j), re and im sharing it.
 //
-// Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).  The
-// leading diagonals p + q = 2, 3, 4 are accumulated in FP32 over K chunks of
-// 64, where every partial sum is an integer multiple of 2^(-8(p+q)) below
-// 2^(24 - 8(p+q)) in magnitude, hence exact; after each chunk they are
-// converted to integers and added into a 64-bit integer per output element.
-// Diagonals 5..7 (weight <= 2^-24 of the leading one) accumulate in FP32
-// over the whole K.  Diagonals > 7 are dropped.  The result is recombined in
-// FP64: C_ij = 2^(E_i + F_j) (S_ij 2^-32 + T_ij).
+// Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).
+// Every slice diagonal g = p + q is accumulated in FP32 over K chunks of 64
+// only, then drained: over one chunk the partial sums of diagonal g are
+// integer multiples of 2^(-8g) whose magnitude stays below 2^24 of those
+// units (at most 6 products of at most 2^15 per k and per real MMA), so the
+// diagonals 2..5 are exact; they are converted to integers and added into
+// one 64-bit integer per output element, S = sum_g d_g 2^(8(5-g)) (|S| <
+// 2^57 for K = 50000).  Diagonals 6 and 7 (weight <= 2^-32 of the leading
+// one) share one FP32 accumulator per chunk, summed across chunks in an FP32
+// register with round-to-nearest.  Diagonals > 7 are dropped.  Keeping
+// every tensor-core accumulation to 64 terms matters: the accumulator
+// truncates toward zero, so an FP32 sum over the whole K would carry a bias
+// growing linearly with K.  The result is recombined in FP64:
+// C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij).
 //
 // Complex arithmetic as two real MMAs per slice pair into one accumulator
 // of 2w columns [re | im]:  Hr x [Yr | Yi]  +  Hi x [-Yi | Yr].
 //
-// Tiling: CTA = 128 rows x 32 complex columns (MMA M = 128, N = 64), K
+// Tiling: CTA = 128 rows x 24 complex columns (MMA M = 128, N = 48), K
 // chunks of 64 (one 128-byte swizzle atom).  Warp 0 issues TMA loads, warp 1
-// issues tcgen05.mma, warps 2..5 drain the exact diagonals each chunk and
-// run the epilogue.  TMEM: 2 x 3 exact accumulators + 1 tail = 448 columns.
+// issues tcgen05.mma, warps 2..9 drain every chunk's accumulators (double
+// buffered in TMEM: 2 x 5 x 48 = 480 columns) and run the epilogue.
 #include <algorithm>
 #include <climits>
 
@@ -42,42 +48,40 @@ namespace {
 constexpr int kBeta = 8;
 constexpr int kS = 6;              // slices per operand (stored)
 constexpr int kBM = 128;           // rows per CTA
-constexpr int kW = 32;             // complex columns per CTA
+constexpr int kW = 24;             // complex columns per CTA
 constexpr int kN = 2 * kW;         // MMA N
 constexpr int kKC = 64;            // K chunk
-constexpr int kAStages = 2;
+constexpr int kAStages = 3;
 constexpr int kBBufs = 2;
 constexpr int kATile = kBM * kKC * 2;                 // 16 KB (one slice part)
 constexpr int kAStageBytes = 2 * kATile;              // Hr_p and Hi_p
-constexpr int kBPart = kW * kKC * 2;                  // 4 KB
+constexpr int kBPart = kW * kKC * 2;                  // 3 KB
 constexpr int kBSlice = 3 * kBPart;                   // [-Yi | Yr | Yi]
-constexpr int kThreads = 192;
+constexpr int kDrainWarps = 8;
+constexpr int kThreads = 64 + 32 * kDrainWarps;       // producer, MMA, drain warps
 constexpr int kTmemCols = 512;
+constexpr int kHalf = kN / 2;                         // columns per drain thread (re or im)
 
-// Variants: slice pairs with p + q <= MAXD are formed; diagonals 2..EXT are
-// accumulated exactly (EXT < 2: none).  FP64 accuracy: (7, 4).  Mixed
-// precision: (4, 1), the first three slices only, all in FP32.
-template <int MAXD, int EXT>
+// Variants: slices 1..NSL of each operand, pairs with p + q <= NSL + 1;
+// diagonals 2..EXT exact, diagonals EXT+1..NSL+1 (if any) in the FP32 tail.
+// FP64 accuracy: (6, 5).  Mixed precision: (4, 5): 32 bits per operand
+// relative to its row/column maximum, every diagonal exact.
+template <int NSL, int EXT>
 struct OzCfg {
-    static constexpr int kSl = MAXD - 1;                       // slices used per operand
-    static constexpr int kNEx = EXT >= 2 ? EXT - 1 : 0;        // exact accumulators
+    static constexpr int kSl = NSL;
+    static constexpr int kMaxD = NSL + 1;
+    static constexpr int kNEx = EXT - 1;                        // exact accumulators
+    static constexpr bool kTail = EXT < NSL + 1;
+    static constexpr int kSlots = kNEx + (kTail ? 1 : 0);       // accumulators per buffer
     static constexpr int kBBufBytes = kSl * kBSlice;
     static constexpr int kSmem = kAStages * kAStageBytes + kBBufs * kBBufBytes + 1024;
-    static constexpr uint32_t kTail = 2 * kNEx * kN;           // TMEM column of the tail
-    // A slices of a chunk are consumed in the order EXT..kSl (pairs only in
-    // the FP32 tail), then 1..EXT-1, so the exact accumulators are complete
-    // early in the chunk.
-    __host__ __device__ static constexpr int order(int idx) {
-        return (EXT <= 1) ? idx + 1 : (idx <= kSl - EXT ? idx + EXT : idx - (kSl - EXT) );
-    }
-    static constexpr int kLastExactSlice = EXT - 1;
+    static constexpr int kEx = EXT;
 };
-using CfgFP64 = OzCfg<7, 4>;
-using CfgMixed = OzCfg<4, 1>;
-static_assert(CfgFP64::order(0) == 4 && CfgFP64::order(2) == 6 && CfgFP64::order(3) == 1 &&
-                  CfgFP64::order(5) == 3,
-              "slice order");
-static_assert(CfgFP64::kSmem <= 232448 && CfgFP64::kTail + kN <= kTmemCols, "resources");
+using CfgFP64 = OzCfg<6, 5>;
+using CfgMixed = OzCfg<4, 5>;
+static_assert(CfgFP64::kSmem <= 232448 && 2 * CfgFP64::kSlots * kN <= kTmemCols, "resources");
+static_assert(CfgMixed::kSmem <= 232448 && 2 * CfgMixed::kSlots * kN <= kTmemCols, "resources");
+static_assert(kN % 16 == 0 && kW % 8 == 0 && kHalf % 8 == 0, "MMA N, TMA box rows, TMEM loads");
 
 __device__ __forceinline__ void split_digits(double x, int E, int *t) {
     // X = rint(x 2^(48 - E)), |X| <= 2^48; balanced base-256 digits
@@ -105,17 +109,22 @@ __device__ __forceinline__ float slice_value(int t, int p) {
 // ----------------------------------------------------------- exponents
 // E[i] = max over the row (rows_are_cols = 0) or column (1) of the frexp
 // exponent of |re| and |im|; INT_MIN for an all-zero line.
+// Non-finite entries cannot be sliced; they are reported through the
+// error word (fmax alone would skip NaN).
 __global__ void k_row_exponent(int64_t N, const z_t *__restrict__ H, int64_t ldh, int *E,
-                               int cols_per_block) {
+                               int cols_per_block, ChaseScalars *sc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int64_t k0 = (int64_t)blockIdx.y * cols_per_block;
     const int64_t k1 = (k0 + cols_per_block < N) ? k0 + cols_per_block : N;
     double mx = 0.0;
+    bool finite = true;
     for (int64_t k = k0; k < k1; k++) {
         const z_t h = H[i + k * ldh];
+        finite = finite && isfinite(h.x) && isfinite(h.y);
         mx = fmax(mx, fmax(fabs(h.x), fabs(h.y)));
     }
+    if (!finite) set_error(sc, DEV_NONFINITE, (int)i);
     if (mx > 0.0) {
         int e;
         frexp(mx, &e);
@@ -123,15 +132,19 @@ __global__ void k_row_exponent(int64_t N, const z_t *__restrict__ H, int64_t ldh
     }
 }
 
-__global__ void k_col_exponent(int64_t N, int n, const z_t *__restrict__ Y, int64_t ldy, int *F) {
+__global__ void k_col_exponent(int64_t N, int n, const z_t *__restrict__ Y, int64_t ldy, int *F,
+                               ChaseScalars *sc) {
     const int j = blockIdx.y;
     if (j >= n) return;
     double mx = 0.0;
+    bool finite = true;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
          k += (int64_t)gridDim.x * blockDim.x) {
         const z_t y = Y[k + j * ldy];
+        finite = finite && isfinite(y.x) && isfinite(y.y);
         mx = fmax(mx, fmax(fabs(y.x), fabs(y.y)));
     }
+    if (!finite) set_error(sc, DEV_NONFINITE, j);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.0) {
         int e;
@@ -215,32 +228,31 @@ struct OzArgs {
     ChaseScalars *sc;
 };
 
-template <class Cfg, int MAXD, int EXT>
+template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               OzArgs args) {
     constexpr int kSl = Cfg::kSl;
+    constexpr int kSlots = Cfg::kSlots;
     constexpr int kBBufBytes = Cfg::kBBufBytes;
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;                                        // kAStages x 32 KB
-    uint8_t *sB = sm + kAStages * kAStageBytes;              // kBBufs x 72 KB
+    uint8_t *sB = sm + kAStages * kAStageBytes;              // kBBufs x slices x 9 KB
     __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kBBufs], emptyB[kBBufs];
-    __shared__ uint64_t exFull[2], exEmpty[2], tailFull;
+    __shared__ uint64_t accFull[2], accEmpty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int jt = blockIdx.x, it = blockIdx.y;
-    const int j0 = jt * kW;
-    const int64_t i0 = (int64_t)it * kBM;
+    const int j0 = blockIdx.x * kW;
+    const int64_t i0 = (int64_t)blockIdx.y * kBM;
     const int nch = args.nchunks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
         for (int s = 0; s < kBBufs; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
-        for (int s = 0; s < 2; s++) { tc::mbar_init(&exFull[s], 1); tc::mbar_init(&exEmpty[s], 4); }
-        tc::mbar_init(&tailFull, 1);
+        for (int s = 0; s < 2; s++) { tc::mbar_init(&accFull[s], 1); tc::mbar_init(&accEmpty[s], kDrainWarps); }
         abort_flag = 0;
         tc::mbar_fence_init();
     }
@@ -249,13 +261,13 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_base;
-    constexpr uint32_t kTail = Cfg::kTail;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
+            const int64_t Np = (int64_t)nch * kKC;
             int use = 0;
             for (int c = 0; c < nch && !abort_flag; c++) {
                 const int bb = c & 1;
@@ -269,13 +281,11 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     tc::tma_load_2d(bdst + q * kBSlice + 2 * kBPart, &tmB, c * kKC, rb + args.mp + j0, &fullB[bb]);
                 }
                 bool ok = true;
-                for (int idx = 0; idx < kSl; idx++, use++) {
-                    const int p = Cfg::order(idx) - 1;
+                for (int p = 0; p < kSl; p++, use++) {
                     const int st = use % kAStages, n = use / kAStages;
                     if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
                     tc::mbar_expect_tx(&fullA[st], kAStageBytes);
                     uint8_t *adst = sA + st * kAStageBytes;
-                    const int64_t Np = (int64_t)nch * kKC;
                     tc::tma_load_2d(adst, &tmA, c * kKC, (int)((p * 2 + 0) * Np + i0), &fullA[st]);
                     tc::tma_load_2d(adst + kATile, &tmA, c * kKC, (int)((p * 2 + 1) * Np + i0), &fullA[st]);
                 }
@@ -286,40 +296,32 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
-            bool tail_started = false;
             int use = 0;
             for (int c = 0; c < nch && !abort_flag; c++) {
-                const int bb = c & 1, ex = c & 1;
+                const int bb = c & 1;
                 if (!tc::mbar_wait(&fullB[bb], (c >> 1) & 1, &abort_flag)) break;
-                if (Cfg::kNEx > 0 && c >= 2 &&
-                    !tc::mbar_wait(&exEmpty[ex], ((c >> 1) - 1) & 1, &abort_flag))
-                    break;
-                bool ex_started[3] = {false, false, false};
+                if (c >= 2 && !tc::mbar_wait(&accEmpty[bb], ((c >> 1) - 1) & 1, &abort_flag)) break;
+                tc::fence_after();
+                bool started[kSlots];
+#pragma unroll
+                for (int s = 0; s < kSlots; s++) started[s] = false;
                 const uint8_t *bsrc = sB + bb * kBBufBytes;
                 bool ok = true;
-                for (int idx = 0; idx < kSl; idx++, use++) {
-                    const int p = Cfg::order(idx);
+                for (int p = 1; p <= kSl; p++, use++) {
                     const int st = use % kAStages, n = use / kAStages;
                     if (!tc::mbar_wait(&fullA[st], n & 1, &abort_flag)) { ok = false; break; }
                     tc::fence_after();
                     const uint8_t *aR = sA + st * kAStageBytes, *aI = aR + kATile;
-                    for (int q = 1; p + q <= MAXD; q++) {
+                    const uint64_t a_r = tc::sdesc_sw128(aR), a_i = tc::sdesc_sw128(aI);
+                    for (int q = 1; p + q <= Cfg::kMaxD; q++) {
                         const int g = p + q;
-                        uint32_t d;
-                        bool acc0;
-                        if (g <= EXT) {
-                            d = tmem + (uint32_t)((ex * Cfg::kNEx + (g - 2)) * kN);
-                            acc0 = ex_started[g - 2];
-                            ex_started[g - 2] = true;
-                        } else {
-                            d = tmem + kTail;
-                            acc0 = tail_started;
-                            tail_started = true;
-                        }
+                        const int slot = (g <= Cfg::kEx) ? g - 2 : kSlots - 1;
+                        const uint32_t d = tmem + (uint32_t)((bb * kSlots + slot) * kN);
+                        const bool acc0 = started[slot];
+                        started[slot] = true;
                         const uint8_t *bq = bsrc + (q - 1) * kBSlice;
                         const uint64_t b_pos = tc::sdesc_sw128(bq + kBPart);   // [Yr | Yi]
                         const uint64_t b_neg = tc::sdesc_sw128(bq);            // [-Yi | Yr]
-                        const uint64_t a_r = tc::sdesc_sw128(aR), a_i = tc::sdesc_sw128(aI);
 #pragma unroll
                         for (int kk = 0; kk < kKC / 16; kk++) {
                             tc::mma_bf16(d, a_r + 2 * kk, b_pos + 2 * kk, idesc, (acc0 || kk > 0) ? 1u : 0u);
@@ -327,76 +329,82 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                     }
                     tc::mma_commit(&emptyA[st]);
-                    if (Cfg::kNEx > 0 && p == Cfg::kLastExactSlice) tc::mma_commit(&exFull[ex]);
                 }
                 if (!ok) break;
                 tc::mma_commit(&emptyB[bb]);
+                tc::mma_commit(&accFull[bb]);
             }
-            tc::mma_commit(&tailFull);
         }
     } else {
         // ------------------------------------------------ drain + epilogue
-        const int quad = warp & 3;
+        // warp w: TMEM lanes of quadrant (w & 3); columns [half*24, half*24+24)
+        // of every accumulator (half 0: re, half 1: im).
+        const int quad = warp & 3, half = (warp - 2) >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-        long long S[kN];
+        long long S[kHalf];
+        float T[kHalf];
 #pragma unroll
-        for (int j = 0; j < kN; j++) S[j] = 0;
+        for (int j = 0; j < kHalf; j++) { S[j] = 0; T[j] = 0.f; }
         bool ok = true;
-        for (int c = 0; Cfg::kNEx > 0 && c < nch; c++) {
-            const int ex = c & 1;
-            if (!tc::mbar_wait(&exFull[ex], (c >> 1) & 1, &abort_flag)) { ok = false; break; }
+        for (int c = 0; c < nch; c++) {
+            const int bb = c & 1;
+            if (!tc::mbar_wait(&accFull[bb], (c >> 1) & 1, &abort_flag)) { ok = false; break; }
             tc::fence_after();
 #pragma unroll
-            for (int g = 2; g <= EXT; g++) {
+            for (int g = 2; g <= Cfg::kEx; g++) {
                 const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
-                const int shift = kBeta * (4 - g);                             // S in units of 2^-32
+                const int shift = kBeta * (5 - g);                             // S in units of 2^-40
+                const uint32_t col = (uint32_t)((bb * kSlots + (g - 2)) * kN + half * kHalf);
+                uint32_t r[kHalf];
 #pragma unroll
-                for (int h = 0; h < kN / 16; h++) {
-                    uint32_t r[16];
-                    tc::tmem_ld16(tmem + lane_addr + (uint32_t)((ex * Cfg::kNEx + (g - 2)) * kN + h * 16), r);
-                    tc::tmem_wait_ld();
+                for (int h = 0; h < kHalf; h += 8) tc::tmem_ld8(tmem + lane_addr + col + h, r + h);
+                tc::tmem_wait_ld();
 #pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const int d = __float2int_rn(__uint_as_float(r[u]) * scale);
-                        S[h * 16 + u] += (long long)d << shift;
-                    }
+                for (int u = 0; u < kHalf; u++) {
+                    const int d = __float2int_rn(__uint_as_float(r[u]) * scale);
+                    S[u] += (long long)d << shift;
                 }
+            }
+            if (Cfg::kTail) {
+                const uint32_t col = (uint32_t)((bb * kSlots + kSlots - 1) * kN + half * kHalf);
+                uint32_t r[kHalf];
+#pragma unroll
+                for (int h = 0; h < kHalf; h += 8) tc::tmem_ld8(tmem + lane_addr + col + h, r + h);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < kHalf; u++) T[u] += __uint_as_float(r[u]);
             }
             tc::fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&exEmpty[ex]);
+            if (lane == 0) tc::mbar_arrive(&accEmpty[bb]);
         }
-        if (ok && tc::mbar_wait(&tailFull, 0, &abort_flag)) {
-            tc::fence_after();
+        if (ok) {
             const int64_t i = i0 + row;
-            int e = (i < args.M) ? args.E[i] : 0;
-            if (e == INT_MIN) e = 0;
+            if (i < args.M) {
+                int e = args.E[i];
+                if (e == INT_MIN) e = 0;
 #pragma unroll
-            for (int h = 0; h < kW / 16; h++) {
-                uint32_t rr[16], ri[16];
-                tc::tmem_ld16(tmem + lane_addr + kTail + h * 16, rr);
-                tc::tmem_ld16(tmem + lane_addr + kTail + kW + h * 16, ri);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < 16; u++) {
-                    const int jl = h * 16 + u, j = j0 + jl;
-                    if (i >= args.M || j >= args.n) continue;
+                for (int u = 0; u < kHalf; u++) {
+                    const int j = j0 + u;
+                    if (j >= args.n) continue;
                     int f = args.F[j];
                     if (f == INT_MIN) f = 0;
-                    const double cr = ldexp((double)S[jl] * 0x1.0p-32 + (double)__uint_as_float(rr[u]), e + f);
-                    const double ci = ldexp((double)S[kW + jl] * 0x1.0p-32 + (double)__uint_as_float(ri[u]), e + f);
-                    z_t v = zmk(cr, ci);
+                    const double v = ldexp((double)S[u] * 0x1.0p-40 + (double)T[u], e + f);
+                    double out = v;
                     if (args.ep.mode == GEMM_CHEB) {
-                        const z_t y = args.Y[i + j * args.ldy];
-                        v = zscale(zsub(v, zscale(y, args.ep.c)), args.ep.s1);
-                        if (args.ep.Yp) v = zsub(v, zscale(args.ep.Yp[i + j * args.ep.ldyp], args.ep.s2));
+                        const double y = half ? args.Y[i + j * args.ldy].y : args.Y[i + j * args.ldy].x;
+                        out = args.ep.s1 * (v - args.ep.c * y);
+                        if (args.ep.Yp) {
+                            const z_t yp = args.ep.Yp[i + j * args.ep.ldyp];
+                            out -= args.ep.s2 * (half ? yp.y : yp.x);
+                        }
                     }
-                    args.C[i + j * args.ldc] = v;
+                    double *cp = (double *)(args.C + i + j * args.ldc);
+                    cp[half] = out;
                 }
             }
         }
-        (void)ok;
     }
 
     tc::fence_before();
@@ -454,7 +462,8 @@ size_t ozaki_b_bytes(int64_t N, int m) {
     return (size_t)kS * 3 * mp * Np * 2;
 }
 
-cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cudaStream_t st) {
+cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
+                            cudaStream_t st) {
     const int64_t Np = ozaki_padded(N);
     oh->N = N;
     oh->Np = Np;
@@ -462,7 +471,7 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cu
     bse_count_launches(1);
     const int cpb = 256;
     dim3 g1((unsigned)((N + 255) / 256), (unsigned)((N + cpb - 1) / cpb));
-    k_row_exponent<<<g1, 256, 0, st>>>(N, H, ldh, oh->E, cpb);
+    k_row_exponent<<<g1, 256, 0, st>>>(N, H, ldh, oh->E, cpb, sc);
     bse_count_launches(1);
     dim3 g2((unsigned)(Np / 32), (unsigned)(Np / 32));
     k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
@@ -472,17 +481,17 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, cu
     return cudaGetLastError();
 }
 
-template <class Cfg, int MAXD, int EXT>
+template <class Cfg>
 cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a,
                            dim3 grid, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_ozaki_zgemm<Cfg, MAXD, EXT>,
+        cudaError_t e = cudaFuncSetAttribute(k_ozaki_zgemm<Cfg>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_ozaki_zgemm<Cfg, MAXD, EXT><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
+    k_ozaki_zgemm<Cfg><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
     bse_count_launches(1);
     return cudaGetLastError();
 }
@@ -496,7 +505,7 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     k_fill_int<<<(mp + 255) / 256, 256, 0, st>>>(F, mp, INT_MIN);
     bse_count_launches(1);
     dim3 ge((unsigned)std::min<int64_t>((N + 255) / 256, 16), (unsigned)n);
-    k_col_exponent<<<ge, 256, 0, st>>>(N, n, Y, ldy, F);
+    k_col_exponent<<<ge, 256, 0, st>>>(N, n, Y, ldy, F, sc);
     bse_count_launches(1);
     dim3 gs((unsigned)((Np + 255) / 256), (unsigned)mp);
     k_slice_y<<<gs, 256, 0, st>>>(N, Np, n, mp, Y, ldy, F, (uint16_t *)bslices);
@@ -519,6 +528,6 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.sc = sc;
     dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM));
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
-    if (low) return launch_variant<CfgMixed, 4, 1>(tmA, tmB, a, grid, st);
-    return launch_variant<CfgFP64, 7, 4>(tmA, tmB, a, grid, st);
+    if (low) return launch_variant<CfgMixed>(tmA, tmB, a, grid, st);
+    return launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
 }

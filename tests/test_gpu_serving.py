@@ -1,0 +1,131 @@
+"""The request server (continuous batching of solves on one GPU): results
+are the same alone and in a concurrent mix, admission follows the HBM
+budget, warm starts reuse resident eigenvectors, and failures (bad or
+over-budget requests, NaN input, time-outs, cancellation) are reported as
+statuses.  Faults are made on the host side only."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2006_08498_gb300 as pkg  # noqa: E402
+
+
+@pytest.fixture
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_08498_gb300 import build
+    build.build()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+GB = 1 << 30
+
+
+def test_alone_equals_mix(ctx):
+    ctx.server_create(64 * GB, 4)
+    R = dict(seed=7, Nk=63, Nv=4, Nc=4, nev=20, nex=10)          # N = 1008
+    alone = ctx.wait(ctx.submit(**R))
+    assert alone["status"] == pkg.BSE_OK
+    mix = [dict(seed=11 + i, Nk=63 + 40 * i, Nv=4, Nc=4, nev=10 + 7 * i, nex=10)
+           for i in range(5)]
+    tickets = [ctx.submit(**r) for r in mix[:3]] + [ctx.submit(**R)] + \
+        [ctx.submit(**r) for r in mix[3:]]
+    res = [ctx.wait(t) for t in tickets]
+    assert all(r["status"] == pkg.BSE_OK for r in res)
+    again = res[3]
+    assert np.array_equal(again["evals"], alone["evals"])
+    assert np.array_equal(again["resid"], alone["resid"])
+    assert again["stats"]["iters"] == alone["stats"]["iters"]
+    # the requests' device work overlapped in time
+    iv = sorted((r["t_start"], r["t_end"]) for r in res)
+    assert any(iv[i + 1][0] < iv[i][1] for i in range(len(iv) - 1))
+    ctx.server_destroy()
+
+
+def test_server_result_equals_direct_solve(ctx):
+    Hd = ctx.build_hamiltonian(3, 63, 4, 4)
+    e, V, r, st = ctx.solve(Hd, 20, 10, seed=3)
+    ctx.server_create(16 * GB, 2)
+    t = ctx.submit(seed=3, Nk=63, Nv=4, Nc=4, nev=20, nex=10)
+    res = ctx.wait(t)
+    assert np.array_equal(res["evals"], e)
+    V2 = ctx.fetch_evecs(t, Hd.shape[0], 20)
+    assert torch.equal(V2, V)
+    ctx.server_destroy()
+
+
+def test_admission_by_budget(ctx):
+    # one N = 2000 request is estimated at ~0.19 GB (H 64 MB, slices of H
+    # 100 MB, search space and workspace): a 0.3 GB budget admits one at a time
+    budget = int(0.3 * GB)
+    ctx.server_create(budget, 4)
+    reqs = [ctx.submit(seed=s, Nk=125, Nv=4, Nc=4, nev=30, nex=15) for s in range(3)]
+    seen_running = 0
+    while any(ctx.poll(t) is None for t in reqs):
+        info = ctx.server_info()
+        seen_running = max(seen_running, info["running"])
+        assert info["held_bytes"] <= budget
+    assert seen_running <= 1
+    res = [ctx.wait(t) for t in reqs]
+    assert all(r["status"] == pkg.BSE_OK for r in res)
+    # strictly sequential execution
+    iv = sorted((r["t_start"], r["t_end"]) for r in res)
+    assert all(iv[i + 1][0] >= iv[i][1] for i in range(len(iv) - 1))
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.submit(seed=1, Nk=500, Nv=4, Nc=4, nev=30, nex=15)   # N = 8000: 1 GB for H alone
+    assert ei.value.status == pkg.BSE_ENOMEM
+    ctx.server_destroy()
+
+
+def test_warm_start_from_resident_eigenvectors(ctx):
+    ctx.server_create(32 * GB, 2)
+    a = ctx.submit(seed=5, Nk=80, Nv=4, Nc=4, nev=30, nex=15)
+    ra = ctx.wait(a)
+    b = ctx.submit(seed=5, Nk=80, Nv=4, Nc=4, nev=30, nex=15, warm_ticket=a)
+    rb = ctx.wait(b)
+    assert rb["status"] == pkg.BSE_OK
+    assert rb["stats"]["iters"] < ra["stats"]["iters"]
+    assert np.allclose(rb["evals"], ra["evals"], rtol=1e-11, atol=0)
+    # a neighbour: slightly different screening strength
+    c = ctx.submit(seed=5, Nk=80, Nv=4, Nc=4, nev=30, nex=15, warm_ticket=a,
+                   model=dict(w0=0.3 * 1.01))
+    rc = ctx.wait(c)
+    assert rc["status"] == pkg.BSE_OK and np.max(rc["resid"]) <= 1e-10
+    ctx.server_destroy()
+
+
+def test_timeout_cancel_and_bad_requests(ctx):
+    ctx.server_create(int(0.45 * GB), 1)
+    t1 = ctx.submit(seed=1, Nk=125, Nv=4, Nc=4, nev=40, nex=20)
+    t2 = ctx.submit(seed=2, Nk=125, Nv=4, Nc=4, nev=40, nex=20)     # queued behind t1
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.wait(t1, timeout_s=1e-4)
+    assert ei.value.status == pkg.BSE_ETIMEOUT
+    assert ctx.release(t2) == pkg.BSE_OK                              # cancel while queued
+    r2 = ctx.wait(t2)
+    assert r2["status"] == pkg.BSE_EINVAL and r2["evals"] is None
+    assert ctx.wait(t1)["status"] == pkg.BSE_OK
+    for bad in (dict(nev=0, nex=5), dict(nev=40, nex=600), dict(nev=10, nex=5, tol=-1.0),
+                dict(nev=10, nex=5, precision=9)):
+        kw = dict(seed=1, Nk=16, Nv=4, Nc=4)
+        kw.update(bad)
+        with pytest.raises(pkg.BseError) as ei:
+            ctx.submit(**kw)
+        assert ei.value.status == pkg.BSE_EINVAL
+    ctx.server_destroy()
+
+
+def test_nan_request_is_reported(ctx):
+    ctx.server_create(16 * GB, 2)
+    t = ctx.submit(seed=1, Nk=40, Nv=4, Nc=4, nev=10, nex=5, model=dict(w0=math.nan))
+    good = ctx.submit(seed=1, Nk=40, Nv=4, Nc=4, nev=10, nex=5)
+    assert ctx.wait(t)["status"] == pkg.BSE_ENONFINITE
+    assert ctx.wait(good)["status"] == pkg.BSE_OK                  # the server keeps serving
+    ctx.server_destroy()
