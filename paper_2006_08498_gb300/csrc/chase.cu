@@ -67,7 +67,7 @@ void release_workspace(bsechase_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
                       &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
                       &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
-                      &ctx->ozB, &ctx->ozF};
+                      &ctx->ozB, &ctx->ozF, &ctx->ozP};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFreeAsync(b->p, ctx->st);
         b->p = nullptr;
@@ -174,6 +174,9 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     const int mc = std::max(max_cols, 32);
     if ((rc = ensure(ctx, ctx->ozB, ozaki_b_bytes(op.N, mc)))) return rc;
     if ((rc = ensure(ctx, ctx->ozF, (size_t)(mc + 64) * sizeof(int)))) return rc;
+    // split-K partials: up to 16 splits of 24 columns, or 2 of the full width
+    const size_t pbytes = (size_t)op.N * 16 * std::max(16 * 24, 2 * (mc + 24));
+    if ((rc = ensure(ctx, ctx->ozP, pbytes))) return rc;
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
     CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
@@ -185,7 +188,7 @@ int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy
               int64_t ldc, const GemmEpi &ep) {
     if (op.tc)
         CK(ozaki_zgemm(ctx->oh, n, Y, ldy, C, ldc, ep, ctx->ozB.p, (int *)ctx->ozF.p, ctx->sc,
-                       op.low ? 1 : 0, ctx->st));
+                       op.low ? 1 : 0, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st));
     else
         CK(launch_zgemm_nn(op.N, n, op.N, op.H, op.ldh, Y, ldy, C, ldc, ep, ctx->st));
     return BSE_OK;
@@ -570,6 +573,8 @@ int bsechase_create(bsechase_ctx **out, int device, void *stream) {
         bsechase_destroy(ctx);
         return BSE_ENOMEM;
     }
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        ctx->sms = 152;
     ctx->ev_ok = true;
     for (int i = 0; i < 8; i++)
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;

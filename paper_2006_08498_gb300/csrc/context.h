@@ -24,7 +24,9 @@ struct bsechase_ctx {
     ChaseScalars *hsc = nullptr;     // pinned host mirror
     // workspace
     DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
-    DevBuf ozA, ozE, ozB, ozF;       // tensor-core products: slices of H and of the operand
+    DevBuf ozA, ozE, ozB, ozF, ozP;  // tensor-core products: slices of H and of the operand,
+                                     // split-K partials
+    int sms = 0;                     // multiprocessors of the device
     OzakiH oh;
     int64_t wsN = 0;
     int wsM = 0;

@@ -57,9 +57,11 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 // F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
 // low = 0: FP64 accuracy (6 slices, 21 slice pairs); low = 1: FP32-level
 // accuracy (the first four slices, 10 pairs, all exact).
+// K is split across CTAs (FP64 partials in `partials`, summed in a fixed
+// order) when that fills the `sms` multiprocessors better.
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
-                        cudaStream_t st);
+                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st);
 
 // ---- vector kernels (vec.cu)
 int vec_partial_blocks(int64_t N);

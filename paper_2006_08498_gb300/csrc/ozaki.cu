@@ -226,6 +226,8 @@ struct OzArgs {
     z_t *C;
     int64_t ldc;
     ChaseScalars *sc;
+    int csplit;       // K chunks per split (gridDim.z splits)
+    z_t *P;           // split > 1: FP64 partial products [z][j][i], ld M
 };
 
 template <class Cfg>
@@ -248,6 +250,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const int j0 = blockIdx.x * kW;
     const int64_t i0 = (int64_t)blockIdx.y * kBM;
     const int nch = args.nchunks;
+    const int c0 = blockIdx.z * args.csplit;
+    const int c1 = min(nch, c0 + args.csplit);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
@@ -269,9 +273,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             tc::prefetch_tmap(&tmB);
             const int64_t Np = (int64_t)nch * kKC;
             int use = 0;
-            for (int c = 0; c < nch && !abort_flag; c++) {
-                const int bb = c & 1;
-                if (c >= 2 && !tc::mbar_wait(&emptyB[bb], ((c >> 1) - 1) & 1, &abort_flag)) break;
+            for (int c = c0; c < c1 && !abort_flag; c++) {
+                const int lc = c - c0, bb = lc & 1;
+                if (lc >= 2 && !tc::mbar_wait(&emptyB[bb], ((lc >> 1) - 1) & 1, &abort_flag)) break;
                 tc::mbar_expect_tx(&fullB[bb], kBBufBytes);
                 uint8_t *bdst = sB + bb * kBBufBytes;
                 for (int q = 0; q < kSl; q++) {
@@ -297,10 +301,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
             int use = 0;
-            for (int c = 0; c < nch && !abort_flag; c++) {
-                const int bb = c & 1;
-                if (!tc::mbar_wait(&fullB[bb], (c >> 1) & 1, &abort_flag)) break;
-                if (c >= 2 && !tc::mbar_wait(&accEmpty[bb], ((c >> 1) - 1) & 1, &abort_flag)) break;
+            for (int c = c0; c < c1 && !abort_flag; c++) {
+                const int lc = c - c0, bb = lc & 1;
+                if (!tc::mbar_wait(&fullB[bb], (lc >> 1) & 1, &abort_flag)) break;
+                if (lc >= 2 && !tc::mbar_wait(&accEmpty[bb], ((lc >> 1) - 1) & 1, &abort_flag)) break;
                 tc::fence_after();
                 bool started[kSlots];
 #pragma unroll
@@ -347,9 +351,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
         for (int j = 0; j < kHalf; j++) { S[j] = 0; T[j] = 0.f; }
         bool ok = true;
-        for (int c = 0; c < nch; c++) {
-            const int bb = c & 1;
-            if (!tc::mbar_wait(&accFull[bb], (c >> 1) & 1, &abort_flag)) { ok = false; break; }
+        for (int c = c0; c < c1; c++) {
+            const int lc = c - c0, bb = lc & 1;
+            if (!tc::mbar_wait(&accFull[bb], (lc >> 1) & 1, &abort_flag)) { ok = false; break; }
             tc::fence_after();
 #pragma unroll
             for (int g = 2; g <= Cfg::kEx; g++) {
@@ -392,6 +396,11 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (f == INT_MIN) f = 0;
                     const double v = ldexp((double)S[u] * 0x1.0p-40 + (double)T[u], e + f);
                     double out = v;
+                    if (args.P) {        // split-K partial; summed and finished by k_split_reduce
+                        double *pp = (double *)(args.P + ((int64_t)blockIdx.z * args.n + j) * args.M + i);
+                        pp[half] = out;
+                        continue;
+                    }
                     if (args.ep.mode == GEMM_CHEB) {
                         const double y = half ? args.Y[i + j * args.ldy].y : args.Y[i + j * args.ldy].x;
                         out = args.ep.s1 * (v - args.ep.c * y);
@@ -414,6 +423,22 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         tc::fence_after();
         tc::tmem_dealloc(tmem, kTmemCols);
     }
+}
+
+// C = epi(sum over splits z of P[z]) in increasing z (deterministic).
+__global__ void k_split_reduce(int64_t M, int n, int nsplit, const z_t *__restrict__ P,
+                               GemmEpi ep, const z_t *__restrict__ Y, int64_t ldy, z_t *C,
+                               int64_t ldc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= M) return;
+    z_t v = zmk(0.0, 0.0);
+    for (int z = 0; z < nsplit; z++) v = zadd(v, P[((int64_t)z * n + j) * M + i]);
+    if (ep.mode == GEMM_CHEB) {
+        v = zscale(zsub(v, zscale(Y[i + j * ldy], ep.c)), ep.s1);
+        if (ep.Yp) v = zsub(v, zscale(ep.Yp[i + j * ep.ldyp], ep.s2));
+    }
+    C[i + j * ldc] = v;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -498,7 +523,7 @@ cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const
 
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
-                        cudaStream_t st) {
+                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int64_t N = oh.N, Np = oh.Np;
     const int mp = (n + kW - 1) / kW * kW;
@@ -526,8 +551,28 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.C = C;
     a.ldc = ldc;
     a.sc = sc;
-    dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM));
+    // split K so that the CTAs fill whole waves of the SMs: the smallest
+    // ceil(tiles * s / sms) / s over s, with at least 16 K chunks per split
+    // and the partials bounded by the workspace
+    const int tiles = (mp / kW) * (int)(Np / kBM);
+    int best = 1;
+    double best_t = 1e30;
+    for (int sp = 1; sp <= 16; sp++) {
+        if ((int64_t)sp * 16 > a.nchunks && sp > 1) break;
+        if ((int64_t)sp * n * N * (int64_t)sizeof(z_t) > partial_bytes && sp > 1) break;
+        const double t = (double)((tiles * sp + sms - 1) / sms) / sp * (1.0 + 0.01 * (sp - 1));
+        if (t < best_t - 1e-12) { best_t = t; best = sp; }
+    }
+    a.csplit = (a.nchunks + best - 1) / best;
+    const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
+    a.P = (nsplit > 1) ? partials : nullptr;
+    dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM), (unsigned)nsplit);
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
-    if (low) return launch_variant<CfgMixed>(tmA, tmB, a, grid, st);
-    return launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
+    cudaError_t e = low ? launch_variant<CfgMixed>(tmA, tmB, a, grid, st)
+                        : launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
+    if (e != cudaSuccess || nsplit == 1) return e;
+    dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
+    k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, partials, ep, Y, ldy, C, ldc);
+    bse_count_launches(1);
+    return cudaGetLastError();
 }
