@@ -159,8 +159,17 @@ __global__ void k_fill_int(int *p, int n, int v) {
 }
 
 // ------------------------------------------------------------ slicing
-// A slices of H (K-major): A[((p*2 + ri)*Np + i)*Np + k] = slice p of
-// re/im H_ik.  32 x 32 tiles through shared memory; padded rows and columns
+// Slices are stored K-chunk-tiled: for matrix `part` (slice and re/im), K
+// chunk kc = k / 64 holds all rows x 64 K-elements contiguously, so the
+// tile a CTA loads (rows x 64) is one contiguous block of memory:
+// index = ((part * nch + kc) * rows + row) * 64 + k % 64.
+__host__ __device__ __forceinline__ int64_t tiled_index(int part, int64_t k, int64_t row,
+                                                       int64_t Kp, int64_t rows) {
+    const int64_t nch = Kp / 64;
+    return (((int64_t)part * nch + k / 64) * rows + row) * 64 + (k % 64);
+}
+
+// A slices of H: slice p of re/im H_ik at tiled_index(p*2 + ri, k, i).  32 x 32 tiles through shared memory; padded rows and columns
 // (>= N) are written as zeros.
 __global__ void k_slice_h(int64_t N, int64_t Np, const z_t *__restrict__ H, int64_t ldh,
                           const int *__restrict__ E, uint16_t *A) {
@@ -182,14 +191,14 @@ __global__ void k_slice_h(int64_t N, int64_t Np, const z_t *__restrict__ H, int6
         split_digits(h.y, e, ti);
 #pragma unroll
         for (int p = 0; p < kS; p++) {
-            A[((int64_t)(p * 2 + 0) * Np + i) * Np + k] = bf16_exact(slice_value(tr[p], p));
-            A[((int64_t)(p * 2 + 1) * Np + i) * Np + k] = bf16_exact(slice_value(ti[p], p));
+            A[tiled_index(p * 2 + 0, k, i, Np, Np)] = bf16_exact(slice_value(tr[p], p));
+            A[tiled_index(p * 2 + 1, k, i, Np, Np)] = bf16_exact(slice_value(ti[p], p));
         }
     }
 }
 
-// B slices of Y (K-major rows): slice q, rows [0, mp) Yr, [mp, 2mp) Yi,
-// [2mp, 3mp) -Yi; B[((q*3 + part)*mp + j)*Np + k].
+// B slices of Y: slice q of Yr, Yi and -Yi (part 0, 1, 2) of column j at
+// tiled_index(q*3 + part, k, j) with mp rows.
 __global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__restrict__ Y,
                           int64_t ldy, const int *__restrict__ F, uint16_t *B) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,9 +215,9 @@ __global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__res
     split_digits(y.y, e, ti);
 #pragma unroll
     for (int q = 0; q < kS; q++) {
-        B[((int64_t)(q * 3 + 0) * mp + j) * Np + k] = bf16_exact(slice_value(tr[q], q));
-        B[((int64_t)(q * 3 + 1) * mp + j) * Np + k] = bf16_exact(slice_value(ti[q], q));
-        B[((int64_t)(q * 3 + 2) * mp + j) * Np + k] = bf16_exact(slice_value(-ti[q], q));
+        B[tiled_index(q * 3 + 0, k, j, Np, mp)] = bf16_exact(slice_value(tr[q], q));
+        B[tiled_index(q * 3 + 1, k, j, Np, mp)] = bf16_exact(slice_value(ti[q], q));
+        B[tiled_index(q * 3 + 2, k, j, Np, mp)] = bf16_exact(slice_value(-ti[q], q));
     }
 }
 
@@ -271,7 +280,6 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if (lane == 0) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
-            const int64_t Np = (int64_t)nch * kKC;
             int use = 0;
             for (int c = c0; c < c1 && !abort_flag; c++) {
                 const int lc = c - c0, bb = lc & 1;
@@ -279,10 +287,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 tc::mbar_expect_tx(&fullB[bb], kBBufBytes);
                 uint8_t *bdst = sB + bb * kBBufBytes;
                 for (int q = 0; q < kSl; q++) {
-                    const int rb = q * 3 * args.mp;
-                    tc::tma_load_2d(bdst + q * kBSlice + 0 * kBPart, &tmB, c * kKC, rb + 2 * args.mp + j0, &fullB[bb]);
-                    tc::tma_load_2d(bdst + q * kBSlice + 1 * kBPart, &tmB, c * kKC, rb + j0, &fullB[bb]);
-                    tc::tma_load_2d(bdst + q * kBSlice + 2 * kBPart, &tmB, c * kKC, rb + args.mp + j0, &fullB[bb]);
+                    // smem [-Yi | Yr | Yi] from parts 2, 0, 1
+                    tc::tma_load_3d(bdst + q * kBSlice + 0 * kBPart, &tmB, 0, j0, (q * 3 + 2) * nch + c, &fullB[bb]);
+                    tc::tma_load_3d(bdst + q * kBSlice + 1 * kBPart, &tmB, 0, j0, (q * 3 + 0) * nch + c, &fullB[bb]);
+                    tc::tma_load_3d(bdst + q * kBSlice + 2 * kBPart, &tmB, 0, j0, (q * 3 + 1) * nch + c, &fullB[bb]);
                 }
                 bool ok = true;
                 for (int p = 0; p < kSl; p++, use++) {
@@ -290,8 +298,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
                     tc::mbar_expect_tx(&fullA[st], kAStageBytes);
                     uint8_t *adst = sA + st * kAStageBytes;
-                    tc::tma_load_2d(adst, &tmA, c * kKC, (int)((p * 2 + 0) * Np + i0), &fullA[st]);
-                    tc::tma_load_2d(adst + kATile, &tmA, c * kKC, (int)((p * 2 + 1) * Np + i0), &fullA[st]);
+                    tc::tma_load_3d(adst, &tmA, 0, (int)i0, (p * 2 + 0) * nch + c, &fullA[st]);
+                    tc::tma_load_3d(adst + kATile, &tmA, 0, (int)i0, (p * 2 + 1) * nch + c, &fullA[st]);
                 }
                 if (!ok) break;
             }
@@ -459,15 +467,16 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor [rows][K] (K contiguous), box of 64 x box_rows, 128-byte swizzle
-bool make_map(CUtensorMap *m, void *base, uint64_t K, uint64_t rows, uint32_t box_rows) {
+// 3-D BF16 tensor of K-chunk tiles [tiles][rows][64], box 64 x box_rows x 1,
+// 128-byte swizzle (the shared-memory image of one K-major rows x 64 tile).
+bool make_map(CUtensorMap *m, void *base, uint64_t rows, uint64_t tiles, uint32_t box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    cuuint64_t dims[2] = {K, rows};
-    cuuint64_t strides[1] = {K * 2};
-    cuuint32_t box[2] = {64, box_rows};
-    cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+    cuuint64_t dims[3] = {64, rows, tiles};
+    cuuint64_t strides[2] = {64 * 2, rows * 64 * 2};
+    cuuint32_t box[3] = {64, box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -501,7 +510,8 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     dim3 g2((unsigned)(Np / 32), (unsigned)(Np / 32));
     k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
     bse_count_launches(1);
-    if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * Np), kBM))
+    if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * (Np / kKC)),
+                  kBM))
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -536,7 +546,7 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     k_slice_y<<<gs, 256, 0, st>>>(N, Np, n, mp, Y, ldy, F, (uint16_t *)bslices);
     bse_count_launches(1);
     CUtensorMap tmB;
-    if (!make_map(&tmB, bslices, (uint64_t)Np, (uint64_t)(kS * 3 * mp), kW))
+    if (!make_map(&tmB, bslices, (uint64_t)mp, (uint64_t)(kS * 3 * (Np / kKC)), kW))
         return cudaErrorInvalidValue;
     OzArgs a;
     a.M = N;
