@@ -15,27 +15,31 @@
 // split the same way per column j (exponent F_j), re and im sharing it.
 //
 // Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).
-// Every slice diagonal g = p + q is accumulated in FP32 over K chunks of 64
-// only, then drained: over one chunk the partial sums of diagonal g are
-// integer multiples of 2^(-8g) whose magnitude stays below 2^24 of those
-// units (at most 6 products of at most 2^15 per k and per real MMA), so the
-// diagonals 2..5 are exact; they are converted to integers and added into
-// one 64-bit integer per output element, S = sum_g d_g 2^(8(5-g)) (|S| <
-// 2^57 for K = 50000).  Diagonals 6 and 7 (weight <= 2^-32 of the leading
-// one) share one FP32 accumulator per chunk, summed across chunks in an FP32
-// register with round-to-nearest.  Diagonals > 7 are dropped.  Keeping
-// every tensor-core accumulation to 64 terms matters: the accumulator
-// truncates toward zero, so an FP32 sum over the whole K would carry a bias
-// growing linearly with K.  The result is recombined in FP64:
-// C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij).
+// The diagonals g = 2..5 are accumulated in FP32 over K chunks of 64 only,
+// then drained: over one chunk the partial sums of diagonal g are integer
+// multiples of 2^(-8g) whose magnitude stays below 2^24 of those units (at
+// most 6 products of at most 2^15 per k and per real MMA), so they are
+// exact; they are converted to integers and added into one 64-bit integer
+// per output element, S = sum_g d_g 2^(8(5-g)) (|S| < 2^57 for K = 50000).
+// Keeping these accumulations to 64 terms matters: the tensor core's FP32
+// accumulator truncates toward zero, so a sum over the whole K would carry a
+// bias growing with K.  Diagonals 6 and 7 (weight <= 2^-32 of the leading
+// one) share one FP32 accumulator over the whole K: its truncation error is
+// at most one FP32 ulp of the running tail sum per K step of 16, i.e. below
+// (K/16) 2^-23 of the tail and about 2^-45 of the leading diagonal's scale
+// for K = 20000.  Diagonals > 7 are dropped.  The result is recombined in
+// FP64: C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij).
 //
 // Complex arithmetic as two real MMAs per slice pair into one accumulator
 // of 2w columns [re | im]:  Hr x [Yr | Yi]  +  Hi x [-Yi | Yr].
 //
-// Tiling: CTA = 128 rows x 24 complex columns (MMA M = 128, N = 48), K
+// Tiling: CTA = 128 rows x 48 complex columns (MMA M = 128, N = 96), K
 // chunks of 64 (one 128-byte swizzle atom).  Warp 0 issues TMA loads, warp 1
-// issues tcgen05.mma, warps 2..9 drain every chunk's accumulators (double
-// buffered in TMEM: 2 x 5 x 48 = 480 columns) and run the epilogue.
+// issues tcgen05.mma, warps 2..9 drain the exact accumulators of every chunk
+// and run the epilogue.  TMEM holds five 96-column accumulators (480 of 512
+// columns): one per exact diagonal and the tail.  An MMA with N <= 128 costs
+// about the same issue time on this tensor core whatever N is, so the widest
+// N that leaves room for five accumulators is the one used.
 #include <algorithm>
 #include <climits>
 
@@ -48,14 +52,12 @@ namespace {
 constexpr int kBeta = 8;
 constexpr int kS = 6;              // slices per operand (stored)
 constexpr int kBM = 128;           // rows per CTA
-constexpr int kW = 24;             // complex columns per CTA
+constexpr int kW = 48;             // complex columns per CTA
 constexpr int kN = 2 * kW;         // MMA N
 constexpr int kKC = 64;            // K chunk
-constexpr int kAStages = 3;
-constexpr int kBBufs = 2;
-constexpr int kATile = kBM * kKC * 2;                 // 16 KB (one slice part)
-constexpr int kAStageBytes = 2 * kATile;              // Hr_p and Hi_p
-constexpr int kBPart = kW * kKC * 2;                  // 3 KB
+constexpr int kAStages = 6;        // A stages of one part (Re or Im of one slice)
+constexpr int kATile = kBM * kKC * 2;                 // 16 KB
+constexpr int kBPart = kW * kKC * 2;                  // 6 KB
 constexpr int kBSlice = 3 * kBPart;                   // [-Yi | Yr | Yi]
 constexpr int kDrainWarps = 8;
 constexpr int kThreads = 64 + 32 * kDrainWarps;       // producer, MMA, drain warps
@@ -69,19 +71,17 @@ constexpr int kHalf = kN / 2;                         // columns per drain threa
 template <int NSL, int EXT>
 struct OzCfg {
     static constexpr int kSl = NSL;
-    static constexpr int kMaxD = NSL + 1;
-    static constexpr int kNEx = EXT - 1;                        // exact accumulators
     static constexpr bool kTail = EXT < NSL + 1;
-    static constexpr int kSlots = kNEx + (kTail ? 1 : 0);       // accumulators per buffer
-    static constexpr int kBBufBytes = kSl * kBSlice;
-    static constexpr int kSmem = kAStages * kAStageBytes + kBBufs * kBBufBytes + 1024;
+    static constexpr int kAcc = (EXT - 1) + (kTail ? 1 : 0);     // TMEM accumulators
+    static constexpr int kSmem = kAStages * kATile + (NSL + 1) * kBSlice + 1024;
     static constexpr int kEx = EXT;
 };
 using CfgFP64 = OzCfg<6, 5>;
 using CfgMixed = OzCfg<4, 5>;
-static_assert(CfgFP64::kSmem <= 232448 && 2 * CfgFP64::kSlots * kN <= kTmemCols, "resources");
-static_assert(CfgMixed::kSmem <= 232448 && 2 * CfgMixed::kSlots * kN <= kTmemCols, "resources");
-static_assert(kN % 16 == 0 && kW % 8 == 0 && kHalf % 8 == 0, "MMA N, TMA box rows, TMEM loads");
+static_assert(CfgFP64::kSmem <= 232448 && CfgFP64::kAcc * kN <= kTmemCols, "resources");
+static_assert(CfgMixed::kSmem <= 232448 && CfgMixed::kAcc * kN <= kTmemCols, "resources");
+static_assert(kN % 16 == 0 && kW % 8 == 0 && kHalf % 16 == 0, "MMA N, TMA box rows, TMEM loads");
+static_assert(kBPart % 1024 == 0 && kATile % 1024 == 0, "128-byte swizzle atoms stay 1024-aligned");
 
 __device__ __forceinline__ void split_digits(double x, int E, int *t) {
     // X = rint(x 2^(48 - E)), |X| <= 2^48; balanced base-256 digits
@@ -239,19 +239,72 @@ struct OzArgs {
     z_t *P;           // split > 1: FP64 partial products [z][j][i], ld M
 };
 
+// Issue order of the TMA producer within one K chunk.  Items: A part pi
+// (pass pi = 2(p-1) + ri: slice p, ri = 0 for Re H, 1 for Im H) and B slice
+// q.  Each load first waits for its buffer to be released by an earlier
+// chunk; issuing the loads in the order of those releases (then of need)
+// keeps one late release from holding back loads that could already go.
+//   A part pi reuses the stage of part pi - kAStages (released after that
+//   pass).  B slice q >= 2 reuses its own buffer, last read in the previous
+//   chunk by the Im pass of p = S + 1 - q (pass 2(S - q) + 1).  B slice 1
+//   alternates between two buffers; its buffer was last read by the final
+//   pass of the chunk before the previous one.
+template <int S>
+struct ProducerOrder {
+    int kind[3 * S] = {};   // 0: A part, 1: B slice
+    int idx[3 * S] = {};    // pass pi, or slice q
+    __host__ __device__ constexpr ProducerOrder() {
+        int wt[3 * S] = {}, need[3 * S] = {};
+        int n = 0;
+        for (int pi = 0; pi < 2 * S; pi++, n++) {
+            kind[n] = 0; idx[n] = pi; wt[n] = pi - kAStages; need[n] = 8 * pi;
+        }
+        for (int q = 1; q <= S; q++, n++) {
+            kind[n] = 1; idx[n] = q;
+            wt[n] = (q == 1) ? -2 * S - 1 : 1 - 2 * q;
+            need[n] = S - q;
+        }
+        for (int i = 1; i < 3 * S; i++)       // insertion sort on (wait, need)
+            for (int j = i; j > 0; j--) {
+                const bool sw = wt[j] < wt[j - 1] ||
+                                (wt[j] == wt[j - 1] && need[j] < need[j - 1]);
+                if (!sw) break;
+                int t = wt[j];
+                wt[j] = wt[j - 1]; wt[j - 1] = t;
+                t = need[j]; need[j] = need[j - 1]; need[j - 1] = t;
+                t = kind[j]; kind[j] = kind[j - 1]; kind[j - 1] = t;
+                t = idx[j]; idx[j] = idx[j - 1]; idx[j - 1] = t;
+            }
+    }
+};
+
+// One CTA: 128 rows x kW complex columns of C over the K chunks
+// [c0, c1).  Per K chunk the MMA warp runs 2S passes, (p, Re H) then
+// (p, Im H) for p = 1..S, and in each pass the slices q = S+1-p down to 1 of
+// Y: accumulator of diagonal g = p + q gets Re H_p x [Yr | Yi]_q (Re pass)
+// and Im H_p x [-Yi | Yr]_q (Im pass), four K=16 MMAs each.  Diagonal g's
+// chunk sum starts at pair (1, g-1) and ends at pair (g-1, 1), so the four
+// exact accumulators are drained in the order g = 2, 3, 4, 5 while later
+// passes run, and each is free again long before the next chunk reaches it.
+// The tail (g >= EXT+1) accumulates over all chunks in its own columns:
+// its weight is at most 2^-32 of the leading diagonal, so the tensor core's
+// truncating FP32 sums there stay far below FP64 rounding of the result.
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               OzArgs args) {
-    constexpr int kSl = Cfg::kSl;
-    constexpr int kSlots = Cfg::kSlots;
-    constexpr int kBBufBytes = Cfg::kBBufBytes;
+    constexpr int S = Cfg::kSl;
+    constexpr int S2 = 2 * S;
+    constexpr int kEx = Cfg::kEx;              // diagonals 2..kEx exact
+    constexpr int kNEx = kEx - 1;              // exact accumulators
+    constexpr bool kTail = Cfg::kTail;
+    constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = sm;                                        // kAStages x 32 KB
-    uint8_t *sB = sm + kAStages * kAStageBytes;              // kBBufs x slices x 9 KB
-    __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kBBufs], emptyB[kBBufs];
-    __shared__ uint64_t accFull[2], accEmpty[2];
+    uint8_t *sA = sm;                                        // kAStages x 16 KB
+    uint8_t *sB = sm + kAStages * kATile;                    // kNB x [-Yi | Yr | Yi]
+    __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kNB], emptyB[kNB];
+    __shared__ uint64_t accFull[kNEx], accEmpty[kNEx], tailFull;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -264,8 +317,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
-        for (int s = 0; s < kBBufs; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
-        for (int s = 0; s < 2; s++) { tc::mbar_init(&accFull[s], 1); tc::mbar_init(&accEmpty[s], kDrainWarps); }
+        for (int s = 0; s < kNB; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
+        for (int s = 0; s < kNEx; s++) { tc::mbar_init(&accFull[s], 1); tc::mbar_init(&accEmpty[s], kDrainWarps); }
+        tc::mbar_init(&tailFull, 1);
         abort_flag = 0;
         tc::mbar_fence_init();
     }
@@ -275,121 +329,141 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     tc::fence_after();
     const uint32_t tmem = tmem_base;
 
+    // B buffer of slice q in local chunk lc, and how many times that buffer
+    // was filled before
+    auto bbuf = [](int q, int lc) { return q == 1 ? ((lc & 1) ? S : 0) : q - 1; };
+    auto buse = [](int q, int lc) { return q == 1 ? (lc >> 1) : lc; };
+
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
             tc::prefetch_tmap(&tmA);
             tc::prefetch_tmap(&tmB);
-            int use = 0;
-            for (int c = c0; c < c1 && !abort_flag; c++) {
-                const int lc = c - c0, bb = lc & 1;
-                if (lc >= 2 && !tc::mbar_wait(&emptyB[bb], ((lc >> 1) - 1) & 1, &abort_flag)) break;
-                tc::mbar_expect_tx(&fullB[bb], kBBufBytes);
-                uint8_t *bdst = sB + bb * kBBufBytes;
-                for (int q = 0; q < kSl; q++) {
-                    // smem [-Yi | Yr | Yi] from parts 2, 0, 1
-                    tc::tma_load_3d(bdst + q * kBSlice + 0 * kBPart, &tmB, 0, j0, (q * 3 + 2) * nch + c, &fullB[bb]);
-                    tc::tma_load_3d(bdst + q * kBSlice + 1 * kBPart, &tmB, 0, j0, (q * 3 + 0) * nch + c, &fullB[bb]);
-                    tc::tma_load_3d(bdst + q * kBSlice + 2 * kBPart, &tmB, 0, j0, (q * 3 + 1) * nch + c, &fullB[bb]);
+            constexpr ProducerOrder<S> order;
+            bool ok = true;
+            for (int c = c0; c < c1 && ok; c++) {
+                const int lc = c - c0;
+#pragma unroll
+                for (int it = 0; it < 3 * S; it++) {
+                    if (order.kind[it] == 0) {
+                        const int pi = order.idx[it];
+                        const int u = S2 * lc + pi, st = u % kAStages, n = u / kAStages;
+                        if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                        tc::mbar_expect_tx(&fullA[st], kATile);
+                        // part (slice p, re/im) = pi in the A tensor's part order
+                        tc::tma_load_3d(sA + st * kATile, &tmA, 0, (int)i0, pi * nch + c, &fullA[st]);
+                    } else {
+                        const int q = order.idx[it];
+                        const int b = bbuf(q, lc), n = buse(q, lc);
+                        if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                        tc::mbar_expect_tx(&fullB[b], kBSlice);
+                        uint8_t *bdst = sB + b * kBSlice;
+                        // smem [-Yi | Yr | Yi] from parts 2, 0, 1
+                        tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, &fullB[b]);
+                        tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, &fullB[b]);
+                        tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, &fullB[b]);
+                    }
                 }
-                bool ok = true;
-                for (int p = 0; p < kSl; p++, use++) {
-                    const int st = use % kAStages, n = use / kAStages;
-                    if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                    tc::mbar_expect_tx(&fullA[st], kAStageBytes);
-                    uint8_t *adst = sA + st * kAStageBytes;
-                    tc::tma_load_3d(adst, &tmA, 0, (int)i0, (p * 2 + 0) * nch + c, &fullA[st]);
-                    tc::tma_load_3d(adst + kATile, &tmA, 0, (int)i0, (p * 2 + 1) * nch + c, &fullA[st]);
-                }
-                if (!ok) break;
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
-            int use = 0;
-            for (int c = c0; c < c1 && !abort_flag; c++) {
-                const int lc = c - c0, bb = lc & 1;
-                if (!tc::mbar_wait(&fullB[bb], (lc >> 1) & 1, &abort_flag)) break;
-                if (lc >= 2 && !tc::mbar_wait(&accEmpty[bb], ((lc >> 1) - 1) & 1, &abort_flag)) break;
-                tc::fence_after();
-                bool started[kSlots];
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
+            bool ok = true;
+            for (int c = c0; c < c1 && ok; c++) {
+                const int lc = c - c0;
 #pragma unroll
-                for (int s = 0; s < kSlots; s++) started[s] = false;
-                const uint8_t *bsrc = sB + bb * kBBufBytes;
-                bool ok = true;
-                for (int p = 1; p <= kSl; p++, use++) {
-                    const int st = use % kAStages, n = use / kAStages;
-                    if (!tc::mbar_wait(&fullA[st], n & 1, &abort_flag)) { ok = false; break; }
+                for (int pi = 0; pi < S2; pi++) {
+                    const int p = pi / 2 + 1, ri = pi & 1;
+                    const int u = S2 * lc + pi, st = u % kAStages;
+                    if (!tc::mbar_wait(&fullA[st], (u / kAStages) & 1, &abort_flag)) { ok = false; break; }
                     tc::fence_after();
-                    const uint8_t *aR = sA + st * kAStageBytes, *aI = aR + kATile;
-                    const uint64_t a_r = tc::sdesc_sw128(aR), a_i = tc::sdesc_sw128(aI);
-                    for (int q = 1; p + q <= Cfg::kMaxD; q++) {
-                        const int g = p + q;
-                        const int slot = (g <= Cfg::kEx) ? g - 2 : kSlots - 1;
-                        const uint32_t d = tmem + (uint32_t)((bb * kSlots + slot) * kN);
-                        const bool acc0 = started[slot];
-                        started[slot] = true;
-                        const uint8_t *bq = bsrc + (q - 1) * kBSlice;
-                        const uint64_t b_pos = tc::sdesc_sw128(bq + kBPart);   // [Yr | Yi]
-                        const uint64_t b_neg = tc::sdesc_sw128(bq);            // [-Yi | Yr]
+                    const uint64_t a0 = tc::sdesc_sw128(sA + st * kATile);
 #pragma unroll
-                        for (int kk = 0; kk < kKC / 16; kk++) {
-                            tc::mma_bf16(d, a_r + 2 * kk, b_pos + 2 * kk, idesc, (acc0 || kk > 0) ? 1u : 0u);
-                            tc::mma_bf16(d, a_i + 2 * kk, b_neg + 2 * kk, idesc, 1u);
+                    for (int q = S + 1 - p; q >= 1; q--) {
+                        const int g = p + q;
+                        const int b = bbuf(q, lc);
+                        if (pi == 0) {
+                            if (!tc::mbar_wait(&fullB[b], buse(q, lc) & 1, &abort_flag)) { ok = false; break; }
+                            if (g <= kEx && lc >= 1 &&
+                                !tc::mbar_wait(&accEmpty[g - 2], (lc - 1) & 1, &abort_flag)) { ok = false; break; }
+                            tc::fence_after();
                         }
+                        const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
+                        const uint8_t *bq = sB + b * kBSlice;
+                        // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
+                        const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
+                        // a fresh sum: every exact diagonal at its first pair
+                        // of the chunk, the tail at its first pair of the CTA
+                        const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
+                                                      : (lc == 0 && pi == 0 && q == S);
+#pragma unroll
+                        for (int kk = 0; kk < kKC / 16; kk++)
+                            tc::mma_bf16(d, a0 + 2 * kk, b0 + 2 * kk, idesc, (fresh && kk == 0) ? 0u : 1u);
                     }
+                    if (!ok) break;
                     tc::mma_commit(&emptyA[st]);
+                    if (ri == 1) {
+                        // last reader of B slice S + 1 - p; last pair of diagonal p + 1
+                        const int qd = S + 1 - p;
+                        tc::mma_commit(&emptyB[bbuf(qd, lc)]);
+                        if (p + 1 <= kEx) tc::mma_commit(&accFull[p - 1]);
+                    }
                 }
-                if (!ok) break;
-                tc::mma_commit(&emptyB[bb]);
-                tc::mma_commit(&accFull[bb]);
             }
+            if (ok && kTail) tc::mma_commit(&tailFull);
         }
     } else {
         // ------------------------------------------------ drain + epilogue
-        // warp w: TMEM lanes of quadrant (w & 3); columns [half*24, half*24+24)
+        // warp w: TMEM lanes of quadrant (w & 3); columns [half*kW, half*kW+kW)
         // of every accumulator (half 0: re, half 1: im).
         const int quad = warp & 3, half = (warp - 2) >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-        long long S[kHalf];
-        float T[kHalf];
+        long long Sx[kHalf];
 #pragma unroll
-        for (int j = 0; j < kHalf; j++) { S[j] = 0; T[j] = 0.f; }
+        for (int j = 0; j < kHalf; j++) Sx[j] = 0;
         bool ok = true;
-        for (int c = c0; c < c1; c++) {
-            const int lc = c - c0, bb = lc & 1;
-            if (!tc::mbar_wait(&accFull[bb], (lc >> 1) & 1, &abort_flag)) { ok = false; break; }
-            tc::fence_after();
+        for (int c = c0; c < c1 && ok; c++) {
+            const int lc = c - c0;
 #pragma unroll
-            for (int g = 2; g <= Cfg::kEx; g++) {
+            for (int g = 2; g <= kEx; g++) {
+                if (!tc::mbar_wait(&accFull[g - 2], lc & 1, &abort_flag)) { ok = false; break; }
+                tc::fence_after();
+                const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
+                uint32_t r[kHalf];
+#pragma unroll
+                for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, r + h);
+                tc::tmem_wait_ld();
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&accEmpty[g - 2]);
                 const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
                 const int shift = kBeta * (5 - g);                             // S in units of 2^-40
-                const uint32_t col = (uint32_t)((bb * kSlots + (g - 2)) * kN + half * kHalf);
-                uint32_t r[kHalf];
-#pragma unroll
-                for (int h = 0; h < kHalf; h += 8) tc::tmem_ld8(tmem + lane_addr + col + h, r + h);
-                tc::tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < kHalf; u++) {
-                    const int d = __float2int_rn(__uint_as_float(r[u]) * scale);
-                    S[u] += (long long)d << shift;
+                    const int dv = __float2int_rn(__uint_as_float(r[u]) * scale);
+                    Sx[u] += (long long)dv << shift;
                 }
             }
-            if (Cfg::kTail) {
-                const uint32_t col = (uint32_t)((bb * kSlots + kSlots - 1) * kN + half * kHalf);
+        }
+        float T[kHalf];
+#pragma unroll
+        for (int j = 0; j < kHalf; j++) T[j] = 0.f;
+        if (ok && kTail) {
+            if (tc::mbar_wait(&tailFull, 0, &abort_flag)) {
+                tc::fence_after();
+                const uint32_t col = (uint32_t)(kNEx * kN + half * kHalf);
                 uint32_t r[kHalf];
 #pragma unroll
-                for (int h = 0; h < kHalf; h += 8) tc::tmem_ld8(tmem + lane_addr + col + h, r + h);
+                for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, r + h);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < kHalf; u++) T[u] += __uint_as_float(r[u]);
+                for (int u = 0; u < kHalf; u++) T[u] = __uint_as_float(r[u]);
+            } else {
+                ok = false;
             }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&accEmpty[bb]);
         }
         if (ok) {
             const int64_t i = i0 + row;
@@ -402,7 +476,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (j >= args.n) continue;
                     int f = args.F[j];
                     if (f == INT_MIN) f = 0;
-                    const double v = ldexp((double)S[u] * 0x1.0p-40 + (double)T[u], e + f);
+                    const double v = ldexp((double)Sx[u] * 0x1.0p-40 + (double)T[u], e + f);
                     double out = v;
                     if (args.P) {        // split-K partial; summed and finished by k_split_reduce
                         double *pp = (double *)(args.P + ((int64_t)blockIdx.z * args.n + j) * args.M + i);
