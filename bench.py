@@ -131,15 +131,16 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "fp64_dfma": 2}
 DTYPES = {"fp64": "f64 (H products: bf16 slices on tensor cores, exact int + f32 accumulation)",
           "mixed": "f64 with f32-level filter sweeps (4 bf16 slices, exact accumulation)",
           "fp64_dfma": "f64"}
-# slice-pair products per complex multiply-add of the tensor-core filter
-PAIRS = {"fp64": 21, "mixed": 10}
-
-
 def roofline(precision, st, N):
-    """Roofline of the dominant kernel (the filter's product), from the
-    library's CUDA-event filter time: FP64-equivalent work 8 N^2 per column
-    product; the tensor-core emulation executes 2 x 2 x 2 real flops per
-    complex multiply-add for each slice pair."""
+    """Roofline of the dominant kernel, the filter's matrix product.
+
+    Tensor-core precisions: the product kernel k_ozaki_zgemm is timed by the
+    library with CUDA events around every launch on its stream, inside this
+    timed region.  Its algorithmic work per launch is 8 N^2 n real flops per
+    slice pair (21 pairs at FP64 accuracy, 10 at FP32 level) for n columns:
+    achieved = summed work / summed launch time, against the measured BF16
+    peak.  DFMA precision: the FP64-equivalent filter rate (8 N^2 per column
+    product over the filter phase) against the measured DFMA peak."""
     peaks = _peaks()
     fp64_eq = st["filter_tflops"]
     tr = _traffic(precision)
@@ -151,19 +152,19 @@ def roofline(precision, st, N):
                 "traffic": (tr or {}).get("bytes_per_launch"),
                 "algorithmic_flops_per_launch_avg":
                     8.0 * N * N * st["filter_matvecs"] / max(1, st["filter_launches"])}
-    low, hi = st["filter_matvecs_low"], st["filter_matvecs"] - st["filter_matvecs_low"]
-    pairs = (PAIRS["mixed"] * low + PAIRS["fp64"] * hi) / max(1, st["filter_matvecs"])
-    achieved = fp64_eq * pairs
+    achieved = st["tc_kernel_tflops"]
     peak = peaks.get("bf16_tflops_sustained") or 1700.0
-    return {"kernel": "k_ozaki_zgemm (filter H*Y, slice products on tcgen05, Chebyshev epilogue)",
+    launches = max(1, st["tc_kernel_launches"])
+    return {"kernel": "k_ozaki_zgemm (H*Y: BF16 slice products on tcgen05, Chebyshev epilogue)",
             "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside "
                             "a seconds-long solve)" if peaks else "fallback 1.7 PFLOP/s sustained"),
             "traffic": (tr or {}).get("bytes_per_launch"),
-            "fp64_equivalent_tflops": fp64_eq, "slice_pairs_per_cmac": pairs,
-            "algorithmic_flops_per_launch_avg":
-                8.0 * pairs * N * N * st["filter_matvecs"] / max(1, st["filter_launches"])}
+            "launches": st["tc_kernel_launches"],
+            "avg_launch_ms": st["tc_kernel_ms"] / launches,
+            "algorithmic_flops_per_launch_avg": achieved * 1e12 * st["tc_kernel_ms"] / 1e3 / launches,
+            "fp64_equivalent_filter_tflops": fp64_eq}
 
 
 def cpu_baseline_sample(W, seconds_budget=25.0):
@@ -304,7 +305,8 @@ def run_ours(args, rank, world, local_rank):
             "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs",
                                          "filter_matvecs_low", "filter_launches", "ms_lanczos",
                                          "ms_filter", "ms_qr", "ms_rr", "ms_resid",
-                                         "ms_total", "filter_tflops")},
+                                         "ms_total", "filter_tflops", "tc_kernel_ms",
+                                         "tc_kernel_launches", "tc_kernel_tflops")},
             "roofline": roof,
             "e2e": None if e2e_s is None else {
                 "value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N * N,

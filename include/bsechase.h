@@ -106,6 +106,12 @@ typedef struct {
     int64_t kernel_launches;   /* CUDA kernels this solve launched            */
     int64_t filter_launches;   /* filter matrix-product launches              */
     int64_t filter_matvecs_low; /* filter products at FP32-level accuracy     */
+    /* The tensor-core product kernel alone (precisions FP64 and MIXED_FP32),
+     * timed with CUDA events around each launch on the solver's stream:    */
+    double tc_kernel_ms;        /* summed launch durations                    */
+    int64_t tc_kernel_launches; /* launches timed                             */
+    double tc_kernel_tflops;    /* executed BF16 tensor flops (8 per complex  */
+                                /* multiply-add per slice pair) / duration    */
 } chase_stats;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`

@@ -60,7 +60,9 @@ class Stats(ctypes.Structure):
                 ("filter_tflops", ctypes.c_double), ("norm_est", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("lower", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64)]
+                ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64),
+                ("tc_kernel_ms", ctypes.c_double), ("tc_kernel_launches", ctypes.c_int64),
+                ("tc_kernel_tflops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

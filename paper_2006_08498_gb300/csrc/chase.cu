@@ -77,6 +77,21 @@ void release_workspace(bsechase_ctx *ctx) {
     ctx->wsM = 0;
 }
 
+void harvest_kernel_times(bsechase_ctx *ctx) {
+    for (size_t i = 0; i + 1 < ctx->kev_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->kev[i], ctx->kev[i + 1]) == cudaSuccess) {
+            ctx->k_ms += ms;
+            ctx->k_flops += ctx->kev_flops[i / 2];
+            ctx->k_launches++;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    ctx->kev_used = 0;
+    ctx->kev_flops.clear();
+}
+
 namespace {
 
 // Small-array layout inside small_d (doubles) and ints.
@@ -152,6 +167,7 @@ int check_device_error(bsechase_ctx *ctx) {
 int sync_scalars(bsechase_ctx *ctx) {
     CK(cudaMemcpyAsync(ctx->hsc, ctx->sc, sizeof(ChaseScalars), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    harvest_kernel_times(ctx);
     return check_device_error(ctx);
 }
 
@@ -183,13 +199,38 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     return BSE_OK;
 }
 
+// Two timing events for the next tensor-core launch (null when no event
+// can be created: the launch then goes untimed).
+void kernel_events(bsechase_ctx *ctx, double flops, cudaEvent_t *e0, cudaEvent_t *e1) {
+    *e0 = *e1 = nullptr;
+    while (ctx->kev.size() < ctx->kev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        ctx->kev.push_back(e);
+    }
+    *e0 = ctx->kev[ctx->kev_used];
+    *e1 = ctx->kev[ctx->kev_used + 1];
+    ctx->kev_used += 2;
+    ctx->kev_flops.resize(ctx->kev_used / 2);
+    ctx->kev_flops.back() = flops;
+}
+
 // C[N x n] = epi(H Y)
 int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy, z_t *C,
               int64_t ldc, const GemmEpi &ep) {
-    if (op.tc)
+    if (op.tc) {
+        // tensor flops: 8 real flops per complex multiply-add for each of
+        // the 21 (FP64) or 10 (FP32-level) slice pairs
+        const double pairs = op.low ? 10.0 : 21.0;
+        cudaEvent_t e0, e1;
+        kernel_events(ctx, 8.0 * pairs * (double)op.N * (double)op.N * n, &e0, &e1);
         CK(ozaki_zgemm(ctx->oh, n, Y, ldy, C, ldc, ep, ctx->ozB.p, (int *)ctx->ozF.p, ctx->sc,
-                       op.low ? 1 : 0, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st));
-    else
+                       op.low ? 1 : 0, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st, e0,
+                       e1));
+    } else
         CK(launch_zgemm_nn(op.N, n, op.N, op.H, op.ldh, Y, ldy, C, ldc, ep, ctx->st));
     return BSE_OK;
 }
@@ -387,6 +428,10 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     z_t *V = (z_t *)ctx->V.p, *B2 = (z_t *)ctx->B2.p, *B3 = (z_t *)ctx->B3.p;
     Timer tm{ctx};
     const int64_t launches0 = bse_launch_count();
+    ctx->kev_used = 0;
+    ctx->kev_flops.clear();
+    ctx->k_ms = ctx->k_flops = 0.0;
+    ctx->k_launches = 0;
     tm.mark(0);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     Hop op{H, N, ldh, precision_uses_tc(precision)};
@@ -485,6 +530,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     CK(launch_phase_normalize(N, nev, d_evecs, ldz, ctx->st));
     tm.mark(3);
     CK(cudaStreamSynchronize(ctx->st));
+    harvest_kernel_times(ctx);
     tm.add(4, 2, 3);
     if (stats) {
         memset(stats, 0, sizeof *stats);
@@ -508,6 +554,9 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         stats->kernel_launches = bse_launch_count() - launches0;
         stats->filter_launches = filter_launches;
         stats->filter_matvecs_low = filter_mv_low;
+        stats->tc_kernel_ms = ctx->k_ms;
+        stats->tc_kernel_launches = ctx->k_launches;
+        stats->tc_kernel_tflops = ctx->k_ms > 0 ? ctx->k_flops / (ctx->k_ms * 1e9) : 0.0;
     }
     if (!converged) return fail(ctx, BSE_ENOCONV, "not converged after max_iter iterations%s");
     return BSE_OK;
@@ -594,6 +643,7 @@ void bsechase_destroy(bsechase_ctx *ctx) {
     if (ctx->hsc) cudaFreeHost(ctx->hsc);
     for (int i = 0; i < 8; i++)
         if (ctx->ev_ok) cudaEventDestroy(ctx->ev[i]);
+    for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->st);
     delete ctx;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bsechase.h"
 #include "kernels.h"
@@ -32,6 +33,13 @@ struct bsechase_ctx {
     int wsM = 0;
     cudaEvent_t ev[8];
     bool ev_ok = false;
+    // CUDA-event timing of every tensor-core product launch: event pairs
+    // recorded on st, read back at the solver's synchronisation points
+    std::vector<cudaEvent_t> kev;
+    std::vector<double> kev_flops;   // tensor flops of each recorded launch
+    size_t kev_used = 0;             // events recorded since the last harvest
+    double k_ms = 0.0, k_flops = 0.0;
+    int64_t k_launches = 0;
     BseServer *server = nullptr;     // request server attached to this context
 };
 
@@ -44,5 +52,8 @@ void release_workspace(bsechase_ctx *ctx);
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
                  z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
+// Add the recorded tensor-core launch times to k_ms / k_flops / k_launches
+// (the stream must have been synchronised) and recycle the events.
+void harvest_kernel_times(bsechase_ctx *ctx);
 // Stop and free the request server of a context (no-op without one).
 void bse_server_shutdown(bsechase_ctx *ctx);

@@ -58,10 +58,13 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 // low = 0: FP64 accuracy (6 slices, 21 slice pairs); low = 1: FP32-level
 // accuracy (the first four slices, 10 pairs, all exact).
 // K is split across CTAs (FP64 partials in `partials`, summed in a fixed
-// order) when that fills the `sms` multiprocessors better.
+// order) when that fills the `sms` multiprocessors better.  When ev0/ev1
+// are given they are recorded on `st` just before and after the
+// tensor-core kernel itself (not the slicing or the split-K sum).
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
-                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st);
+                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
+                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 // ---- vector kernels (vec.cu)
 int vec_partial_blocks(int64_t N);

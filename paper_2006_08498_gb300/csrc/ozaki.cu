@@ -380,27 +380,43 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (!tc::mbar_wait(&fullA[st], (u / kAStages) & 1, &abort_flag)) { ok = false; break; }
                     tc::fence_after();
                     const uint64_t a0 = tc::sdesc_sw128(sA + st * kATile);
+                    // kk outer, q inner: the MMAs of one K step share their A
+                    // tile, read from shared memory once into the collector
+                    // buffer and reused for every slice q of Y
 #pragma unroll
-                    for (int q = S + 1 - p; q >= 1; q--) {
-                        const int g = p + q;
-                        const int b = bbuf(q, lc);
-                        if (pi == 0) {
-                            if (!tc::mbar_wait(&fullB[b], buse(q, lc) & 1, &abort_flag)) { ok = false; break; }
-                            if (g <= kEx && lc >= 1 &&
-                                !tc::mbar_wait(&accEmpty[g - 2], (lc - 1) & 1, &abort_flag)) { ok = false; break; }
-                            tc::fence_after();
+                    for (int kk = 0; kk < kKC / 16; kk++) {
+#pragma unroll
+                        for (int q = S + 1 - p; q >= 1; q--) {
+                            const int g = p + q;
+                            const int b = bbuf(q, lc);
+                            if (pi == 0 && kk == 0) {
+                                if (!tc::mbar_wait(&fullB[b], buse(q, lc) & 1, &abort_flag)) { ok = false; break; }
+                                if (g <= kEx && lc >= 1 &&
+                                    !tc::mbar_wait(&accEmpty[g - 2], (lc - 1) & 1, &abort_flag)) { ok = false; break; }
+                                tc::fence_after();
+                            }
+                            const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
+                            const uint8_t *bq = sB + b * kBSlice;
+                            // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
+                            const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
+                            // a fresh sum: every exact diagonal at its first pair
+                            // of the chunk, the tail at its first pair of the CTA
+                            const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
+                                                          : (lc == 0 && pi == 0 && q == S);
+                            const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
+                            const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
+                            // no collector in the chunk's first pass, whose MMAs
+                            // wait on barriers between them, nor for a single pair
+                            if (pi == 0 || p == S)
+                                tc::mma_bf16(d, a, bd, idesc, acc);
+                            else if (q == S + 1 - p)
+                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                            else if (q == 1)
+                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                            else
+                                tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
                         }
-                        const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
-                        const uint8_t *bq = sB + b * kBSlice;
-                        // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
-                        const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
-                        // a fresh sum: every exact diagonal at its first pair
-                        // of the chunk, the tail at its first pair of the CTA
-                        const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
-                                                      : (lc == 0 && pi == 0 && q == S);
-#pragma unroll
-                        for (int kk = 0; kk < kKC / 16; kk++)
-                            tc::mma_bf16(d, a0 + 2 * kk, b0 + 2 * kk, idesc, (fresh && kk == 0) ? 0u : 1u);
+                        if (!ok) break;
                     }
                     if (!ok) break;
                     tc::mma_commit(&emptyA[st]);
@@ -607,7 +623,8 @@ cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const
 
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
-                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st) {
+                        z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
+                        cudaEvent_t ev0, cudaEvent_t ev1) {
     if (n <= 0) return cudaSuccess;
     const int64_t N = oh.N, Np = oh.Np;
     const int mp = (n + kW - 1) / kW * kW;
@@ -652,8 +669,10 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.P = (nsplit > 1) ? partials : nullptr;
     dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM), (unsigned)nsplit);
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
+    if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = low ? launch_variant<CfgMixed>(tmA, tmB, a, grid, st)
                         : launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
+    if (ev1) cudaEventRecord(ev1, st);
     if (e != cudaSuccess || nsplit == 1) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
     k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, partials, ep, Y, ldy, C, ldc);

@@ -103,99 +103,41 @@ k_trinv(int n, const z_t *__restrict__ R, int64_t ldr, z_t *X, int64_t ldx) {
     }
 }
 
-// --------------------------------------------- tridiagonal implicit QR
-// Implicit symmetric QR with Wilkinson shift and deflation on the real
-// tridiagonal (d[0..n-1], e[0..n-2]); rotations are collected per sweep
-// by thread 0 and applied by all threads to the rows of Z (row-major
-// n x n; may be null).  Returns 0 or -1 (no convergence).
-__device__ int tridiag_qr_block(int n, double *d, double *e, double *Z, double *cs, int *ctl) {
-    const double eps = 0x1.0p-52;
-    // ctl[0] = state (0 run sweep, 1 done, 2 failed), ctl[1] = p, ctl[2] = q
-    if (threadIdx.x == 0) { ctl[0] = 0; ctl[3] = n - 1; ctl[4] = 0; }
-    __syncthreads();
-    while (true) {
-        if (threadIdx.x == 0) {
-            int q = ctl[3], sweeps = ctl[4];
-            int state = 1;
-            while (q > 0) {
-                if (fabs(e[q - 1]) <= eps * (fabs(d[q - 1]) + fabs(d[q]))) {
-                    e[q - 1] = 0.0;
-                    q--;
-                    sweeps = 0;
-                    continue;
-                }
-                state = 0;
-                break;
-            }
-            if (state == 0) {
-                int p = q - 1;
-                while (p > 0 && fabs(e[p - 1]) > eps * (fabs(d[p - 1]) + fabs(d[p]))) p--;
-                if (p > 0) e[p - 1] = 0.0;
-                if (++sweeps > 60) {
-                    state = 2;
-                } else {
-                    const double hd = (d[q - 1] - d[q]) / 2.0, bq = e[q - 1];
-                    const double den = hd + copysign(hypot(hd, bq), hd);
-                    const double mu = (den != 0.0) ? d[q] - bq * bq / den : d[q] - fabs(bq);
-                    double x = d[p] - mu, z = e[p];
-                    for (int k = p; k < q; k++) {
-                        const double r = hypot(x, z);
-                        const double c = (r == 0.0) ? 1.0 : x / r;
-                        const double s = (r == 0.0) ? 0.0 : -z / r;
-                        if (k > p) e[k - 1] = r;
-                        const double ak = d[k], ak1 = d[k + 1], bk = e[k];
-                        d[k] = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
-                        d[k + 1] = s * s * ak + 2.0 * c * s * bk + c * c * ak1;
-                        e[k] = c * s * (ak - ak1) + (c * c - s * s) * bk;
-                        if (k < q - 1) {
-                            x = e[k];
-                            z = -s * e[k + 1];
-                            e[k + 1] = c * e[k + 1];
-                        }
-                        cs[2 * (k - p)] = c;
-                        cs[2 * (k - p) + 1] = s;
-                    }
-                    ctl[1] = p;
-                    ctl[2] = q;
-                }
-            }
-            ctl[0] = state;
-            ctl[3] = q;
-            ctl[4] = sweeps;
-        }
-        __syncthreads();
-        const int state = ctl[0];
-        if (state != 0) {
-            __syncthreads();
-            return state == 1 ? 0 : -1;
-        }
-        if (Z) {
-            const int p = ctl[1], q = ctl[2];
-            for (int row = threadIdx.x; row < n; row += blockDim.x) {
-                double *zr = Z + (int64_t)row * n;
-                for (int k = p; k < q; k++) {
-                    const double c = cs[2 * (k - p)], s = cs[2 * (k - p) + 1];
-                    const double zk = zr[k], zk1 = zr[k + 1];
-                    zr[k] = c * zk - s * zk1;
-                    zr[k + 1] = s * zk + c * zk1;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------- Hermitian eigensolver
+// G = Q D Z Lambda Z^T D^H Q^H in four launches:
+//   k_heev_reduce  (1 CTA)   Householder reduction to Hermitian tridiagonal
+//                            form, Q = H_0 ... H_{n-2}, and the diagonal
+//                            phases D that make it real: T' = D^H T D;
+//   k_heev_chase   (1 thread) implicit symmetric QR with Wilkinson shift and
+//                            deflation (Golub & Van Loan, Sec. 8.3) on T',
+//                            eigenvalues only; the Givens rotations of every
+//                            sweep are written to a log;
+//   k_heev_rotate  (n/32 CTAs) replays the log on the rows of Z = I;
+//   k_heev_back    (n/4 CTAs) ascending order and Y = Q D Z, one warp per
+//                            column.
+// FP64 issue is slow on this part (one SM does about 1.6 FP64 FMA per
+// clock, and a dependent FP64 operation takes tens of clocks), so the serial
+// chase keeps its dependent chain short and leaves all O(n^2)-per-sweep
+// work to the rotation replay, and the O(n^3) parts run on many SMs where
+// they can.
 struct HeevWork {
     z_t *V;        // n x n Householder vectors (column k from row k+1)
     double *tau;   // n
     z_t *esub;     // n   complex subdiagonal of T
     z_t *delta;    // n   phases
     z_t *p;        // n
-    double *d, *e; // n, n
+    double *d, *e; // n, n: the real tridiagonal; d holds the eigenvalues after the chase
     double *Z;     // n x n real, row-major
-    int *rank;     // n
+    int2 *sweeps;  // (p, q) of every sweep
+    double2 *rot;  // (c, s) of every rotation, sweep after sweep
+    int *nsweeps;  // 1
 };
+
+// Log capacity: sweeps <= 60 n (the per-eigenvalue sweep limit), rotations
+// <= 12 n^2 (the QR iteration with Wilkinson shift takes about 2 sweeps per
+// eigenvalue, i.e. about n^2 rotations; more is reported as no convergence).
+__host__ __device__ inline int64_t heev_max_sweeps(int n) { return 60 * (int64_t)n; }
+__host__ __device__ inline int64_t heev_max_rot(int n) { return 12 * (int64_t)n * n + 4096; }
 
 __host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -211,21 +153,20 @@ __host__ __device__ inline HeevWork heev_layout(int n, void *base) {
     w.d = (double *)p; p += align256(n * sizeof(double));
     w.e = (double *)p; p += align256(n * sizeof(double));
     w.Z = (double *)p; p += align256(nn * sizeof(double));
-    w.rank = (int *)p; p += align256(n * sizeof(int));
+    w.sweeps = (int2 *)p; p += align256(heev_max_sweeps(n) * sizeof(int2));
+    w.rot = (double2 *)p; p += align256(heev_max_rot(n) * sizeof(double2));
+    w.nsweeps = (int *)p; p += align256(sizeof(int));
     return w;
 }
 
 __global__ void __launch_bounds__(kST)
-k_heev(int n, z_t *A, int64_t lda, double *wout, z_t *Y, int64_t ldy, HeevWork w,
-       ChaseScalars *sc) {
+k_heev_reduce(int n, z_t *A, int64_t lda, HeevWork w) {
     __shared__ double red[kSW];
-    __shared__ double cs[2 * kMaxN];
-    __shared__ int ctl[8];
     __shared__ double s_tau, s_K;
     __shared__ z_t s_beta;
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
 
-    // (1) Householder reduction: trailing block B = A[k+1:, k+1:]
+    // Householder reduction: trailing block B = A[k+1:, k+1:]
     for (int k = 0; k + 1 < n; k++) {
         const int L = n - k - 1;
         const z_t *x = A + (k + 1) + (int64_t)k * lda;
@@ -273,65 +214,173 @@ k_heev(int n, z_t *A, int64_t lda, double *wout, z_t *Y, int64_t ldy, HeevWork w
         __syncthreads();
         for (int i = tid; i < L; i += kST) w.p[i] = zsub(w.p[i], zscale(v[i], s_K));
         __syncthreads();
-        // B -= v q^H + q v^H
-        for (int64_t e2 = tid; e2 < (int64_t)L * L; e2 += kST) {
-            const int i = (int)(e2 % L), j = (int)(e2 / L);
-            const z_t vi = v[i], qi = w.p[i], vj = v[j], qj = w.p[j];
-            z_t b = B[i + (int64_t)j * lda];
-            b = zsub(b, zmul(vi, zconj(qj)));
-            b = zsub(b, zmul(qi, zconj(vj)));
-            B[i + (int64_t)j * lda] = b;
+        // B -= v q^H + q v^H: computed on the lower triangle (column j by warp,
+        // rows i >= j by lane) and mirrored to the upper one
+        for (int j = warp; j < L; j += kSW) {
+            const z_t vj = v[j], qj = w.p[j];
+            for (int i = j + lane; i < L; i += 32) {
+                const z_t vi = v[i], qi = w.p[i];
+                z_t b = B[i + (int64_t)j * lda];
+                b = zsub(b, zmul(vi, zconj(qj)));
+                b = zsub(b, zmul(qi, zconj(vj)));
+                if (i == j) b.y = 0.0;
+                B[i + (int64_t)j * lda] = b;
+                if (i != j) B[j + (int64_t)i * lda] = zconj(b);
+            }
         }
         __syncthreads();
     }
-    // (2) real tridiagonal T' = D^H T D
+    // real tridiagonal T' = D^H T D
+    for (int k = tid; k < n; k += kST) {
+        w.d[k] = A[k + (int64_t)k * lda].x;
+        w.e[k] = (k + 1 < n) ? sqrt(zabs2(w.esub[k])) : 0.0;
+    }
+    __syncthreads();
     if (tid == 0) {
         w.delta[0] = zmk(1.0, 0.0);
-        for (int k = 0; k < n; k++) w.d[k] = A[k + (int64_t)k * lda].x;
         for (int k = 0; k + 1 < n; k++) {
-            const double ae = sqrt(zabs2(w.esub[k]));
-            w.e[k] = ae;
+            const double ae = w.e[k];
             w.delta[k + 1] = (ae > 0.0) ? zmul(w.delta[k], zscale(w.esub[k], 1.0 / ae)) : w.delta[k];
         }
     }
-    for (int64_t e2 = tid; e2 < (int64_t)n * n; e2 += kST) w.Z[e2] = (e2 % (n + 1) == 0) ? 1.0 : 0.0;
-    __syncthreads();
-    // (3) implicit QR
-    if (tridiag_qr_block(n, w.d, w.e, w.Z, cs, ctl) != 0) {
-        if (tid == 0) set_error(sc, DEV_EIG_NOCONV, n);
-        return;
-    }
-    // (4) ascending order: stable rank
-    for (int i = tid; i < n; i += kST) {
-        const double di = w.d[i];
-        int r = 0;
-        for (int j = 0; j < n; j++) {
-            const double dj = w.d[j];
-            r += (dj < di) || (dj == di && j < i);
+}
+
+// Implicit QR on the real tridiagonal (one thread).  d and e live in shared
+// memory; the d[k], e[k] of the current chase step are carried in registers.
+// A rotation is taken from rsqrt(x^2 + z^2): entries here are bounded by
+// the norm of the reduced matrix, so the squares neither overflow nor lose
+// anything that matters to the deflation test.
+__global__ void k_heev_chase(int n, HeevWork w, ChaseScalars *sc) {
+    __shared__ double d[kMaxN], e[kMaxN];
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < n; k++) { d[k] = w.d[k]; e[k] = w.e[k]; }
+    const double eps = 0x1.0p-52;
+    const int64_t max_sw = heev_max_sweeps(n), max_rot = heev_max_rot(n);
+    int64_t nsw = 0, nrot = 0;
+    int q = n - 1, sweeps = 0;
+    bool failed = false;
+    while (q > 0) {
+        if (fabs(e[q - 1]) <= eps * (fabs(d[q - 1]) + fabs(d[q]))) {
+            e[q - 1] = 0.0;
+            q--;
+            sweeps = 0;
+            continue;
         }
-        w.rank[i] = r;
-        wout[r] = di;
+        int p = q - 1;
+        while (p > 0 && fabs(e[p - 1]) > eps * (fabs(d[p - 1]) + fabs(d[p]))) p--;
+        if (p > 0) e[p - 1] = 0.0;
+        if (++sweeps > 60 || nsw >= max_sw || nrot + (q - p) > max_rot) {
+            failed = true;
+            break;
+        }
+        const double hd = (d[q - 1] - d[q]) / 2.0, bq = e[q - 1];
+        const double den = hd + copysign(hypot(hd, bq), hd);
+        const double mu = (den != 0.0) ? d[q] - bq * bq / den : d[q] - fabs(bq);
+        w.sweeps[nsw++] = make_int2(p, q);
+        double2 *rl = w.rot + nrot;
+        nrot += q - p;
+        double x = d[p] - mu, z = e[p];
+        double ak = d[p], bk = e[p];
+        for (int k = p; k < q; k++) {
+            const double ak1 = d[k + 1];
+            const double en = (k < q - 1) ? e[k + 1] : 0.0;
+            const double t2 = fma(x, x, z * z);
+            double c = 1.0, sn = 0.0, r = 0.0;
+            if (t2 > 0x1.0p-1000) {
+                const double ir = rsqrt(t2);
+                c = x * ir;
+                sn = -z * ir;
+                r = t2 * ir;
+            } else if (t2 > 0.0) {       // tiny: the scaled form
+                r = hypot(x, z);
+                c = x / r;
+                sn = -z / r;
+            }
+            if (k > p) e[k - 1] = r;
+            const double cc = c * c, ss = sn * sn, cs = c * sn;
+            const double csb = 2.0 * cs * bk;
+            d[k] = fma(cc, ak, fma(ss, ak1, -csb));
+            const double dk1 = fma(ss, ak, fma(cc, ak1, csb));
+            const double ek = fma(cs, ak - ak1, (cc - ss) * bk);
+            e[k] = ek;
+            if (k < q - 1) {
+                x = ek;
+                z = -sn * en;
+                bk = c * en;
+            }
+            ak = dk1;
+            rl[k - p] = make_double2(c, sn);
+        }
+        d[q] = ak;
     }
-    __syncthreads();
-    // (5) vectors: column rank[c] of Y = Q D Z[:, c], Q = H_0 H_1 ... H_{n-2}
-    for (int c = warp; c < n; c += kSW) {
-        z_t *y = Y + (int64_t)w.rank[c] * ldy;
-        for (int i = lane; i < n; i += 32) y[i] = zscale(w.delta[i], w.Z[(int64_t)i * n + c]);
+    for (int k = 0; k < n; k++) w.d[k] = d[k];
+    *w.nsweeps = failed ? -1 : (int)nsw;
+    if (failed) set_error(sc, DEV_EIG_NOCONV, n);
+}
+
+// Z = I, then every logged rotation applied to the rows of Z: lane = row.
+// The CTA's 32 rows sit in shared memory as Zs[k][lane].
+__global__ void __launch_bounds__(32) k_heev_rotate(int n, HeevWork w) {
+    extern __shared__ double Zs[];
+    const int lane = threadIdx.x, row = blockIdx.x * 32 + lane;
+    const int nsw = *w.nsweeps;
+    if (nsw < 0) return;
+    for (int k = 0; k < n; k++) Zs[k * 32 + lane] = (k == row) ? 1.0 : 0.0;
+    __syncwarp();
+    const double2 *rot = w.rot;
+    for (int s = 0; s < nsw; s++) {
+        const int2 pq = w.sweeps[s];
+        const int p = pq.x, q = pq.y;
+        double carry = Zs[p * 32 + lane];
+#pragma unroll 4
+        for (int k = p; k < q; k++) {
+            const double2 r = rot[k - p];
+            const double zk1 = Zs[(k + 1) * 32 + lane];
+            Zs[k * 32 + lane] = r.x * carry - r.y * zk1;
+            carry = fma(r.y, carry, r.x * zk1);
+        }
+        Zs[q * 32 + lane] = carry;
+        rot += q - p;
+    }
+    __syncwarp();
+    if (row < n)
+        for (int k = 0; k < n; k++) w.Z[(int64_t)row * n + k] = Zs[k * 32 + lane];
+}
+
+// Eigenvalues ascending (stable rank) and column rank[c] of Y = Q D Z[:, c];
+// one warp per column c, its vector in shared memory.
+__global__ void __launch_bounds__(128)
+k_heev_back(int n, HeevWork w, double *wout, z_t *Y, int64_t ldy) {
+    __shared__ z_t ys[4][kMaxN];
+    const int lane = threadIdx.x % 32, wl = threadIdx.x / 32;
+    const int c = blockIdx.x * 4 + wl;
+    if (c >= n || *w.nsweeps < 0) return;
+    const double dc = w.d[c];
+    int r = 0;
+    for (int j = lane; j < n; j += 32) {
+        const double dj = w.d[j];
+        r += (dj < dc) || (dj == dc && j < c);
+    }
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    z_t *y = ys[wl];
+    for (int i = lane; i < n; i += 32) y[i] = zscale(w.delta[i], w.Z[(int64_t)i * n + c]);
+    __syncwarp();
+    for (int k = n - 2; k >= 0; k--) {
+        const double t = w.tau[k];
+        if (t == 0.0) continue;
+        const z_t *v = w.V + (k + 1) + (int64_t)k * n;
+        const int L = n - k - 1;
+        z_t s = zmk(0.0, 0.0);
+        for (int i = lane; i < L; i += 32) zcfma(s, v[i], y[k + 1 + i]);
+        s.x = warp_sum(s.x);
+        s.y = warp_sum(s.y);
+        s = zscale(s, t);
+        for (int i = lane; i < L; i += 32) y[k + 1 + i] = zsub(y[k + 1 + i], zmul(s, v[i]));
         __syncwarp();
-        for (int k = n - 2; k >= 0; k--) {
-            const double t = w.tau[k];
-            if (t == 0.0) continue;
-            const z_t *v = w.V + (k + 1) + (int64_t)k * n;
-            const int L = n - k - 1;
-            z_t s = zmk(0.0, 0.0);
-            for (int i = lane; i < L; i += 32) zcfma(s, v[i], y[k + 1 + i]);
-            s.x = warp_sum(s.x);
-            s.y = warp_sum(s.y);
-            s = zscale(s, t);
-            for (int i = lane; i < L; i += 32) y[k + 1 + i] = zsub(y[k + 1 + i], zmul(s, v[i]));
-            __syncwarp();
-        }
     }
+    z_t *yo = Y + (int64_t)r * ldy;
+    for (int i = lane; i < n; i += 32) yo[i] = y[i];
+    if (lane == 0) wout[r] = dc;
 }
 
 // ------------------------------------------------- Lanczos estimate
@@ -506,15 +555,28 @@ size_t heev_work_bytes(int n) {
     const size_t nn = (size_t)n * n;
     return align256(nn * sizeof(z_t)) + align256(n * sizeof(double)) +
            3 * align256(n * sizeof(z_t)) + 2 * align256(n * sizeof(double)) +
-           align256(nn * sizeof(double)) + align256(n * sizeof(int));
+           align256(nn * sizeof(double)) + align256(heev_max_sweeps(n) * sizeof(int2)) +
+           align256(heev_max_rot(n) * sizeof(double2)) + align256(sizeof(int));
 }
 
 cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t ldy, void *work,
                         ChaseScalars *sc, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (n > kMaxN) return cudaErrorInvalidValue;
-    k_heev<<<1, kST, 0, st>>>(n, A, lda, w, Y, ldy, heev_layout(n, work), sc);
-    bse_count_launches(1);
+    const HeevWork hw = heev_layout(n, work);
+    k_heev_reduce<<<1, kST, 0, st>>>(n, A, lda, hw);
+    k_heev_chase<<<1, 32, 0, st>>>(n, hw, sc);
+    const size_t zs = (size_t)32 * n * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_heev_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             32 * kMaxN * (int)sizeof(double));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_heev_rotate<<<(n + 31) / 32, 32, zs, st>>>(n, hw);
+    k_heev_back<<<(n + 3) / 4, 128, 0, st>>>(n, hw, w, Y, ldy);
+    bse_count_launches(4);
     return cudaGetLastError();
 }
 

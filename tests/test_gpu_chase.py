@@ -260,6 +260,28 @@ def test_rayleigh_ritz_matches_oracle(ctx, precision):
     assert np.linalg.norm(A @ V_g - HV_g) <= 1e-12 * np.linalg.norm(HV_g)
 
 
+@pytest.mark.parametrize("n", [280, 512])
+def test_rayleigh_ritz_full_space_degenerate(ctx, n):
+    """Q spanning the whole space: the Ritz pairs are eigenpairs of A.  The
+    spectrum has exact triple eigenvalues and a tight cluster, so the small
+    eigensolver's vectors are not unique; they must still be orthonormal
+    eigenvectors, and the values must match the exact ones."""
+    r = np.random.default_rng(n)
+    lam = np.sort(np.concatenate([np.repeat(r.uniform(0.5, 12.0, n // 8), 3),
+                                  1.0 + 1e-9 * np.arange(n - 3 * (n // 8))]))
+    X = r.standard_normal((n, n)) + 1j * r.standard_normal((n, n))
+    U, _ = np.linalg.qr(X)
+    A = np.asfortranarray(((U * lam) @ U.conj().T + ((U * lam) @ U.conj().T).conj().T) / 2)
+    Q = orthonormal(n, n, n + 1)
+    th_g, Vd, HVd, res = ctx.rayleigh_ritz(dev(A), dev(Q), norm=12.0,
+                                           precision=pkg.CHASE_FP64_DFMA)
+    V_g = host(Vd)
+    assert np.max(np.abs(th_g - lam)) <= 1e-12 * 12.0
+    assert np.linalg.norm(V_g.conj().T @ V_g - np.eye(n)) <= 1e-11
+    R = A @ V_g - V_g * th_g
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-11 * 12.0
+
+
 # ---------------------------------------------------------------- solve
 
 def _check_solution(H, evals, V, resid, nev, w_exact=None, ref=None):
