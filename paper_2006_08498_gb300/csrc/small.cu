@@ -104,33 +104,46 @@ k_trinv(int n, const z_t *__restrict__ R, int64_t ldr, z_t *X, int64_t ldx) {
 }
 
 // ------------------------------------------------- Hermitian eigensolver
-// G = Q D Z Lambda Z^T D^H Q^H in four launches:
-//   k_heev_reduce  (1 CTA)   Householder reduction to Hermitian tridiagonal
-//                            form, Q = H_0 ... H_{n-2}, and the diagonal
-//                            phases D that make it real: T' = D^H T D;
-//   k_heev_chase   (1 thread) implicit symmetric QR with Wilkinson shift and
-//                            deflation (Golub & Van Loan, Sec. 8.3) on T',
-//                            eigenvalues only; the Givens rotations of every
-//                            sweep are written to a log;
-//   k_heev_rotate  (n/32 CTAs) replays the log on the rows of Z = I;
+// G = Q D Z Lambda Z^T D^H Q^H:
+//   k_heev_reduce  (1 CTA)    Householder reduction to Hermitian tridiagonal
+//                             form, Q = H_0 ... H_{n-2}, and the diagonal
+//                             phases D that make it real: T' = D^H T D;
+//   k_heev_tri     (n CTAs)   eigenvalue j of T' by multisection on Sturm
+//                             counts (the 32 lanes of a warp count at 32
+//                             points per step), then its eigenvector from a
+//                             twisted factorization of T' - lambda I (one
+//                             step of inverse iteration from the best unit
+//                             vector; Dhillon & Parlett, 2004), on the
+//                             unreduced block of T' that holds j;
+//   k_heev_gram / k_heev_ns   one Newton-Schulz step Z <- Z (3I - Z^T Z)/2
+//                             (n^3 work spread over SMs), which restores
+//                             orthogonality lost between close eigenvalues;
+//   k_heev_check              residuals |T' z - lambda z| of every column;
+//   k_heev_chase / k_heev_rotate  only when a residual check failed (near
+//                             multiple eigenvalues inside one unreduced
+//                             block): implicit symmetric QR with Wilkinson
+//                             shift (Golub & Van Loan, Sec. 8.3) on one
+//                             thread, its rotations logged and replayed on
+//                             the rows of Z across CTAs;
 //   k_heev_back    (n/4 CTAs) ascending order and Y = Q D Z, one warp per
-//                            column.
-// FP64 issue is slow on this part (one SM does about 1.6 FP64 FMA per
-// clock, and a dependent FP64 operation takes tens of clocks), so the serial
-// chase keeps its dependent chain short and leaves all O(n^2)-per-sweep
-// work to the rotation replay, and the O(n^3) parts run on many SMs where
-// they can.
+//                             column.
+// FP64 issue is slow on this part (one SM does about 2 FP64 FMA per clock,
+// shared by its warps), so the work is spread over many SMs wherever it can
+// be and the serial parts keep their FP64 instruction count small.
 struct HeevWork {
     z_t *V;        // n x n Householder vectors (column k from row k+1)
     double *tau;   // n
     z_t *esub;     // n   complex subdiagonal of T
     z_t *delta;    // n   phases
     z_t *p;        // n
-    double *d, *e; // n, n: the real tridiagonal; d holds the eigenvalues after the chase
-    double *Z;     // n x n real, row-major
-    int2 *sweeps;  // (p, q) of every sweep
+    double *d, *e; // n, n: the real tridiagonal
+    double *lam;   // n   eigenvalues (position order)
+    double *Z;     // n x n real, row-major: eigenvector j in column j
+    double *S1, *S2;  // n x n scratch
+    int2 *sweeps;  // (p, q) of every sweep (fallback path)
     double2 *rot;  // (c, s) of every rotation, sweep after sweep
     int *nsweeps;  // 1
+    int *flag;     // 1: a residual check failed, take the QR path
 };
 
 // Log capacity: sweeps <= 60 n (the per-eigenvalue sweep limit), rotations
@@ -152,11 +165,23 @@ __host__ __device__ inline HeevWork heev_layout(int n, void *base) {
     w.p = (z_t *)p; p += align256(n * sizeof(z_t));
     w.d = (double *)p; p += align256(n * sizeof(double));
     w.e = (double *)p; p += align256(n * sizeof(double));
+    w.lam = (double *)p; p += align256(n * sizeof(double));
     w.Z = (double *)p; p += align256(nn * sizeof(double));
+    w.S1 = (double *)p; p += align256(nn * sizeof(double));
+    w.S2 = (double *)p; p += align256(nn * sizeof(double));
     w.sweeps = (int2 *)p; p += align256(heev_max_sweeps(n) * sizeof(int2));
     w.rot = (double2 *)p; p += align256(heev_max_rot(n) * sizeof(double2));
     w.nsweeps = (int *)p; p += align256(sizeof(int));
+    w.flag = (int *)p; p += align256(sizeof(int));
     return w;
+}
+
+__host__ __device__ inline size_t heev_bytes(int n) {
+    const size_t nn = (size_t)n * n;
+    return align256(nn * sizeof(z_t)) + align256(n * sizeof(double)) +
+           3 * align256(n * sizeof(z_t)) + 3 * align256(n * sizeof(double)) +
+           3 * align256(nn * sizeof(double)) + align256(heev_max_sweeps(n) * sizeof(int2)) +
+           align256(heev_max_rot(n) * sizeof(double2)) + 2 * align256(sizeof(int));
 }
 
 __global__ void __launch_bounds__(kST)
@@ -245,6 +270,203 @@ k_heev_reduce(int n, z_t *A, int64_t lda, HeevWork w) {
     }
 }
 
+// Deflation test shared by every path: e_k is negligible next to its
+// diagonal neighbours.
+__device__ __forceinline__ bool tri_split(const double *d, const double *e, int k) {
+    return fabs(e[k]) <= 0x1.0p-52 * (fabs(d[k]) + fabs(d[k + 1]));
+}
+
+// Number of eigenvalues below x of the unreduced block d[0..nb), e2[0..nb-1)
+// (Sturm count with the pivots q_k of the LDL^T factorization of T - x I).
+__device__ __forceinline__ int sturm_count(int nb, const double *d, const double *e2, double x,
+                                           double pivmin) {
+    double q = d[0] - x;
+    if (fabs(q) < pivmin) q = -pivmin;
+    int c = q < 0.0;
+    for (int k = 1; k < nb; k++) {
+        q = (d[k] - x) - e2[k - 1] / q;
+        if (fabs(q) < pivmin) q = -pivmin;
+        c += q < 0.0;
+    }
+    return c;
+}
+
+// Eigenpair j (j = position in T', i.e. local index j - start of the
+// unreduced block that holds position j).  One warp per CTA.
+__global__ void __launch_bounds__(32) k_heev_tri(int n, HeevWork w) {
+    __shared__ double sd[kMaxN], se[kMaxN], se2[kMaxN];
+    const int j = blockIdx.x, lane = threadIdx.x;
+    if (j == 0 && lane == 0) *w.flag = 0;
+    for (int k = lane; k < n; k += 32) {
+        sd[k] = w.d[k];
+        se[k] = (k + 1 < n) ? w.e[k] : 0.0;
+    }
+    __syncwarp();
+    // the unreduced block [bs, be) holding j
+    int bs = 0, be = n;
+    for (int k = lane; k + 1 < n; k += 32) {
+        if (tri_split(sd, se, k)) {
+            if (k < j) bs = max(bs, k + 1);
+            else be = min(be, k + 1);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bs = max(bs, __shfl_xor_sync(0xffffffffu, bs, o));
+        be = min(be, __shfl_xor_sync(0xffffffffu, be, o));
+    }
+    const int nb = be - bs, li = j - bs;
+    const double *d = sd + bs;
+    double emax = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double ek = (k >= bs && k + 1 < be) ? se[k] : 0.0;
+        se2[k] = ek * ek;
+        emax = fmax(emax, fabs(ek));
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    __syncwarp();
+    const double *e2 = se2 + bs;
+    const double pivmin = 0x1.0p-1000 * fmax(1.0, emax * emax);
+    // Gershgorin interval of the block
+    double lo = INFINITY, hi = -INFINITY;
+    for (int k = lane; k < nb; k += 32) {
+        const double r = (k > 0 ? sqrt(e2[k - 1]) : 0.0) + (k + 1 < nb ? sqrt(e2[k]) : 0.0);
+        lo = fmin(lo, d[k] - r);
+        hi = fmax(hi, d[k] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double widen = 0x1.0p-50 * fmax(fabs(lo), fabs(hi)) + 2.0 * pivmin;
+    double a = lo - widen, b = hi + widen;
+    // multisection: 32 points per step, the interval shrinks 33-fold
+    for (int it = 0; it < 24; it++) {
+        if (b - a <= 0x1.0p-52 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
+        const double h = (b - a) / 33.0;
+        const double x = a + (lane + 1) * h;
+        const int c = sturm_count(nb, d, e2, x, pivmin);
+        const unsigned above = __ballot_sync(0xffffffffu, c > li);
+        if (above == 0u) {
+            a = a + 32.0 * h;
+        } else {
+            const int l = __ffs(above) - 1;
+            const double bn = a + (l + 1) * h;
+            a = (l > 0) ? a + l * h : a;
+            b = bn;
+        }
+    }
+    const double lam = 0.5 * (a + b);
+    if (lane != 0) return;
+    w.lam[j] = lam;
+    // twisted factorization of T' - lam I on the block: L+ D+ L+^T from the
+    // top (multipliers in S1, pivots in S2), U- D- U-^T from the bottom,
+    // twist index r = argmin |gamma_k|
+    double *lk = w.S1, *dp = w.S2, *z = w.Z;
+    const int64_t ld = n;
+    double piv = d[0] - lam;
+    for (int k = 0; k < nb; k++) {
+        if (fabs(piv) < pivmin) piv = -pivmin;
+        dp[(int64_t)(bs + k) * ld + j] = piv;
+        if (k + 1 < nb) {
+            const double ek = se[bs + k];
+            const double l = ek / piv;
+            lk[(int64_t)(bs + k) * ld + j] = l;
+            piv = (d[k + 1] - lam) - l * ek;
+        }
+    }
+    double dm = d[nb - 1] - lam;
+    if (fabs(dm) < pivmin) dm = -pivmin;
+    int r = nb - 1;
+    double gmin = fabs(dp[(int64_t)(be - 1) * ld + j]);   // gamma_{nb-1} = dp_{nb-1}
+    // u_k (k >= 1) stored in z[k] until the vector pass overwrites it
+    for (int k = nb - 2; k >= 0; k--) {
+        const double ek = se[bs + k];
+        const double u = ek / dm;
+        z[(int64_t)(bs + k + 1) * ld + j] = u;
+        dm = (d[k] - lam) - u * ek;
+        if (fabs(dm) < pivmin) dm = -pivmin;
+        const double g = fabs(dp[(int64_t)(bs + k) * ld + j] + dm - (d[k] - lam));
+        if (g < gmin) { gmin = g; r = k; }
+    }
+    // z_r = 1; z_k = -l_k z_{k+1} above r, z_k = -u_k z_{k-1} below r
+    double nrm = 1.0, zk = 1.0;
+    for (int k = r - 1; k >= 0; k--) {
+        zk = -lk[(int64_t)(bs + k) * ld + j] * zk;
+        z[(int64_t)(bs + k) * ld + j] = zk;
+        nrm = fma(zk, zk, nrm);
+    }
+    z[(int64_t)(bs + r) * ld + j] = 1.0;
+    zk = 1.0;
+    for (int k = r + 1; k < nb; k++) {
+        zk = -z[(int64_t)(bs + k) * ld + j] * zk;
+        z[(int64_t)(bs + k) * ld + j] = zk;
+        nrm = fma(zk, zk, nrm);
+    }
+    const double inv = 1.0 / sqrt(nrm);
+    for (int k = 0; k < n; k++) {
+        const int64_t ix = (int64_t)k * ld + j;
+        z[ix] = (k >= bs && k < be) ? z[ix] * inv : 0.0;
+    }
+}
+
+// M = Z^T Z (S1 = M; 16 x 16 tiles of M per 256-thread CTA)
+__global__ void __launch_bounds__(256) k_heev_gram(int n, HeevWork w) {
+    const int r = blockIdx.y * 16 + threadIdx.y, c = blockIdx.x * 16 + threadIdx.x;
+    if (*w.flag) return;
+    if (r >= n || c >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s = fma(w.Z[(int64_t)k * n + r], w.Z[(int64_t)k * n + c], s);
+    w.S1[(int64_t)r * n + c] = s;
+}
+
+// S2 = Z (3 I - M) / 2, one Newton-Schulz step towards the orthogonal polar
+// factor of Z
+__global__ void __launch_bounds__(256) k_heev_ns(int n, HeevWork w) {
+    const int r = blockIdx.y * 16 + threadIdx.y, c = blockIdx.x * 16 + threadIdx.x;
+    if (*w.flag) return;
+    if (r >= n || c >= n) return;
+    double s = 0.0;
+    for (int k = 0; k < n; k++) s = fma(w.Z[(int64_t)r * n + k], w.S1[(int64_t)k * n + c], s);
+    w.S2[(int64_t)r * n + c] = 1.5 * w.Z[(int64_t)r * n + c] - 0.5 * s;
+}
+
+// Every column of S2 must pass |T' z - lam z|_inf <= tol |T'| and
+// | |z|^2 - 1 | <= tol; any failure (or a NaN) raises the flag for the QR
+// path.  After one Newton-Schulz step the orthogonality error E satisfies
+// |E_ij| <= sqrt(E_ii E_jj) to leading order, so the column norms bound it
+// (identical vectors, from eigenvalues equal to working precision inside
+// one block, come out as zero columns and fail here).  One warp per column.
+__global__ void __launch_bounds__(128) k_heev_check(int n, HeevWork w, double tol) {
+    const int lane = threadIdx.x % 32, c = blockIdx.x * 4 + threadIdx.x / 32;
+    if (c >= n) return;
+    const double lam = w.lam[c];
+    double tn = 0.0, res = 0.0, nrm = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double em = k > 0 ? w.e[k - 1] : 0.0, ek = k + 1 < n ? w.e[k] : 0.0;
+        tn = fmax(tn, fabs(w.d[k]) + fabs(em) + fabs(ek));
+        const double zk = w.S2[(int64_t)k * n + c];
+        double t = (w.d[k] - lam) * zk;
+        if (k > 0) t += em * w.S2[(int64_t)(k - 1) * n + c];
+        if (k + 1 < n) t += ek * w.S2[(int64_t)(k + 1) * n + c];
+        res = fmax(res, fabs(t));
+        if (!(t == t)) res = INFINITY;
+        nrm = fma(zk, zk, nrm);
+    }
+    nrm = warp_sum(nrm);
+    for (int o = 16; o > 0; o >>= 1) {
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+        res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+    }
+    if (lane == 0 && !(res <= tol * tn && fabs(nrm - 1.0) <= tol)) atomicExch(w.flag, 1);
+}
+
+// Z <- S2 once every column passed
+__global__ void __launch_bounds__(256) k_heev_accept(int n, HeevWork w) {
+    if (*w.flag) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (int64_t)n * n) w.Z[i] = w.S2[i];
+}
+
 // Implicit QR on the real tridiagonal (one thread).  d and e live in shared
 // memory; the d[k], e[k] of the current chase step are carried in registers.
 // A rotation is taken from rsqrt(x^2 + z^2): entries here are bounded by
@@ -252,7 +474,7 @@ k_heev_reduce(int n, z_t *A, int64_t lda, HeevWork w) {
 // anything that matters to the deflation test.
 __global__ void k_heev_chase(int n, HeevWork w, ChaseScalars *sc) {
     __shared__ double d[kMaxN], e[kMaxN];
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || !*w.flag) return;
     for (int k = 0; k < n; k++) { d[k] = w.d[k]; e[k] = w.e[k]; }
     const double eps = 0x1.0p-52;
     const int64_t max_sw = heev_max_sweeps(n), max_rot = heev_max_rot(n);
@@ -313,7 +535,7 @@ __global__ void k_heev_chase(int n, HeevWork w, ChaseScalars *sc) {
         }
         d[q] = ak;
     }
-    for (int k = 0; k < n; k++) w.d[k] = d[k];
+    for (int k = 0; k < n; k++) w.lam[k] = d[k];
     *w.nsweeps = failed ? -1 : (int)nsw;
     if (failed) set_error(sc, DEV_EIG_NOCONV, n);
 }
@@ -323,6 +545,7 @@ __global__ void k_heev_chase(int n, HeevWork w, ChaseScalars *sc) {
 __global__ void __launch_bounds__(32) k_heev_rotate(int n, HeevWork w) {
     extern __shared__ double Zs[];
     const int lane = threadIdx.x, row = blockIdx.x * 32 + lane;
+    if (!*w.flag) return;
     const int nsw = *w.nsweeps;
     if (nsw < 0) return;
     for (int k = 0; k < n; k++) Zs[k * 32 + lane] = (k == row) ? 1.0 : 0.0;
@@ -354,11 +577,11 @@ k_heev_back(int n, HeevWork w, double *wout, z_t *Y, int64_t ldy) {
     __shared__ z_t ys[4][kMaxN];
     const int lane = threadIdx.x % 32, wl = threadIdx.x / 32;
     const int c = blockIdx.x * 4 + wl;
-    if (c >= n || *w.nsweeps < 0) return;
-    const double dc = w.d[c];
+    if (c >= n || (*w.flag && *w.nsweeps < 0)) return;
+    const double dc = w.lam[c];
     int r = 0;
     for (int j = lane; j < n; j += 32) {
-        const double dj = w.d[j];
+        const double dj = w.lam[j];
         r += (dj < dc) || (dj == dc && j < c);
     }
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
@@ -551,13 +774,7 @@ cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, 
     return cudaGetLastError();
 }
 
-size_t heev_work_bytes(int n) {
-    const size_t nn = (size_t)n * n;
-    return align256(nn * sizeof(z_t)) + align256(n * sizeof(double)) +
-           3 * align256(n * sizeof(z_t)) + 2 * align256(n * sizeof(double)) +
-           align256(nn * sizeof(double)) + align256(heev_max_sweeps(n) * sizeof(int2)) +
-           align256(heev_max_rot(n) * sizeof(double2)) + align256(sizeof(int));
-}
+size_t heev_work_bytes(int n) { return heev_bytes(n); }
 
 cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t ldy, void *work,
                         ChaseScalars *sc, cudaStream_t st) {
@@ -565,6 +782,12 @@ cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t l
     if (n > kMaxN) return cudaErrorInvalidValue;
     const HeevWork hw = heev_layout(n, work);
     k_heev_reduce<<<1, kST, 0, st>>>(n, A, lda, hw);
+    k_heev_tri<<<n, 32, 0, st>>>(n, hw);
+    const dim3 tg((n + 15) / 16, (n + 15) / 16), tb(16, 16);
+    k_heev_gram<<<tg, tb, 0, st>>>(n, hw);
+    k_heev_ns<<<tg, tb, 0, st>>>(n, hw);
+    k_heev_check<<<(n + 3) / 4, 128, 0, st>>>(n, hw, 64.0 * 0x1.0p-52 * n);
+    k_heev_accept<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, st>>>(n, hw);
     k_heev_chase<<<1, 32, 0, st>>>(n, hw, sc);
     const size_t zs = (size_t)32 * n * sizeof(double);
     static bool attr = false;
@@ -576,7 +799,7 @@ cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t l
     }
     k_heev_rotate<<<(n + 31) / 32, 32, zs, st>>>(n, hw);
     k_heev_back<<<(n + 3) / 4, 128, 0, st>>>(n, hw, w, Y, ldy);
-    bse_count_launches(4);
+    bse_count_launches(9);
     return cudaGetLastError();
 }
 
