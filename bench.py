@@ -50,16 +50,19 @@ def _fp64_peak():
         return 1.25, "datasheet (no measured FP64 peak recorded)"
 
 
-def _traffic(precision):
+def _traffic(precision, workload_name):
     """DRAM bytes per launch of the filter kernel from an ncu capture, when
     profiles/filter_traffic_<precision>.txt records one for the current
-    kernel (JSON: {"bytes_per_launch": ...})."""
+    kernel on this workload (JSON: {"bytes_per_launch": ..., "workload": ...})."""
     p = os.path.join(ROOT, "profiles", "filter_traffic_%s.txt" % precision)
     try:
         with open(p) as f:
-            return json.load(f)
+            d = json.load(f)
     except (OSError, ValueError):
         return None
+    if not str(d.get("workload", "")).startswith(workload_name):
+        return None
+    return d
 
 
 class Clocks:
@@ -131,7 +134,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "fp64_dfma": 2}
 DTYPES = {"fp64": "f64 (H products: bf16 slices on tensor cores, exact int + f32 accumulation)",
           "mixed": "f64 with f32-level filter sweeps (4 bf16 slices, exact accumulation)",
           "fp64_dfma": "f64"}
-def roofline(precision, st, N):
+def roofline(precision, st, N, workload_name):
     """Roofline of the dominant kernel, the filter's matrix product.
 
     Tensor-core precisions: the product kernel k_ozaki_zgemm is timed by the
@@ -143,7 +146,7 @@ def roofline(precision, st, N):
     product over the filter phase) against the measured DFMA peak."""
     peaks = _peaks()
     fp64_eq = st["filter_tflops"]
-    tr = _traffic(precision)
+    tr = _traffic(precision, workload_name)
     if precision == "fp64_dfma":
         peak, src = _fp64_peak()
         return {"kernel": "zgemm_nn_kernel (filter H*Y, Chebyshev epilogue, DFMA)",
@@ -293,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         st = stats[-1]
         sec = ms_max / 1e3 / args.steps
-        roof = roofline(args.precision, st, N)
+        roof = roofline(args.precision, st, N, W["workload"])
         line = {
             "metric": METRIC, "value": sec, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
