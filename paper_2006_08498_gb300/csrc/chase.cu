@@ -190,8 +190,7 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     const int mc = std::max(max_cols, 32);
     if ((rc = ensure(ctx, ctx->ozB, ozaki_b_bytes(op.N, mc)))) return rc;
     if ((rc = ensure(ctx, ctx->ozF, (size_t)(mc + 64) * sizeof(int)))) return rc;
-    // split-K partials: up to 16 splits of 24 columns, or 2 of the full width
-    const size_t pbytes = (size_t)op.N * 16 * std::max(16 * 24, 2 * (mc + 24));
+    const size_t pbytes = ozaki_partial_bytes(op.N, mc);
     if ((rc = ensure(ctx, ctx->ozP, pbytes))) return rc;
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;

@@ -50,6 +50,8 @@ struct OzakiH {
 int64_t ozaki_padded(int64_t N);
 size_t ozaki_a_bytes(int64_t N);
 size_t ozaki_b_bytes(int64_t N, int m);
+// workspace for split-K partial products of up to m columns
+size_t ozaki_partial_bytes(int64_t N, int m);
 // Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
 cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
                             cudaStream_t st);

@@ -229,14 +229,10 @@ struct OzArgs {
     int nchunks;      // Np / kKC
     const int *E;     // row exponents of H (padded to Np)
     const int *F;     // column exponents of Y
-    GemmEpi ep;
-    const z_t *Y;     // FP64 operand (for the CHEB epilogue)
-    int64_t ldy;
-    z_t *C;
-    int64_t ldc;
     ChaseScalars *sc;
-    int csplit;       // K chunks per split (gridDim.z splits)
-    z_t *P;           // split > 1: FP64 partial products [z][j][i], ld M
+    int csplit;       // K chunks per split
+    int tx, ty, tz;   // work units: column tiles x row tiles x splits
+    z_t *P;           // FP64 partial products of the splits [z][j][i], ld M
 };
 
 // Issue order of the TMA producer within one K chunk.  Items: A part pi
@@ -278,15 +274,23 @@ struct ProducerOrder {
     }
 };
 
-// One CTA: 128 rows x kW complex columns of C over the K chunks
-// [c0, c1).  Per K chunk the MMA warp runs 2S passes, (p, Re H) then
-// (p, Im H) for p = 1..S, and in each pass the slices q = S+1-p down to 1 of
-// Y: accumulator of diagonal g = p + q gets Re H_p x [Yr | Yi]_q (Re pass)
-// and Im H_p x [-Yi | Yr]_q (Im pass), four K=16 MMAs each.  Diagonal g's
-// chunk sum starts at pair (1, g-1) and ends at pair (g-1, 1), so the four
-// exact accumulators are drained in the order g = 2, 3, 4, 5 while later
-// passes run, and each is free again long before the next chunk reaches it.
-// The tail (g >= EXT+1) accumulates over all chunks in its own columns:
+// A persistent kernel: one CTA per SM walks the work units u = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  A unit is 128 rows x kW complex columns of C
+// over the K chunks of one split, numbered column tile fastest, then row
+// tile, then split (so the CTAs running at one time share the operand slices
+// of one K range in L2).  TMEM, the barriers and the pipelines live for the
+// whole launch: the next unit's loads and MMAs start while the previous one
+// drains, and no SM waits between CTAs.  Every role counts the chunks it has
+// processed (gc) and the units (uc), and all barrier phases follow from them.
+//
+// Per K chunk the MMA warp runs 2S passes, (p, Re H) then (p, Im H) for
+// p = 1..S, and in each pass the slices q = S+1-p down to 1 of Y:
+// accumulator of diagonal g = p + q gets Re H_p x [Yr | Yi]_q (Re pass) and
+// Im H_p x [-Yi | Yr]_q (Im pass), four K=16 MMAs each.  Diagonal g's chunk
+// sum starts at pair (1, g-1) and ends at pair (g-1, 1), so the four exact
+// accumulators are drained in the order g = 2, 3, 4, 5 while later passes
+// run, and each is free again long before the next chunk reaches it.  The
+// tail (g >= EXT+1) accumulates over the unit's chunks in its own columns:
 // its weight is at most 2^-32 of the leading diagonal, so the tensor core's
 // truncating FP32 sums there stay far below FP64 rounding of the result.
 template <class Cfg>
@@ -304,22 +308,20 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint8_t *sA = sm;                                        // kAStages x 16 KB
     uint8_t *sB = sm + kAStages * kATile;                    // kNB x [-Yi | Yr | Yi]
     __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kNB], emptyB[kNB];
-    __shared__ uint64_t accFull[kNEx], accEmpty[kNEx], tailFull;
+    __shared__ uint64_t accFull[kNEx], accEmpty[kNEx], tailFull, tailEmpty;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int j0 = blockIdx.x * kW;
-    const int64_t i0 = (int64_t)blockIdx.y * kBM;
     const int nch = args.nchunks;
-    const int c0 = blockIdx.z * args.csplit;
-    const int c1 = min(nch, c0 + args.csplit);
+    const int units = args.tx * args.ty * args.tz;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
         for (int s = 0; s < kNB; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
         for (int s = 0; s < kNEx; s++) { tc::mbar_init(&accFull[s], 1); tc::mbar_init(&accEmpty[s], kDrainWarps); }
         tc::mbar_init(&tailFull, 1);
+        tc::mbar_init(&tailEmpty, kDrainWarps);
         abort_flag = 0;
         tc::mbar_fence_init();
     }
@@ -329,10 +331,19 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     tc::fence_after();
     const uint32_t tmem = tmem_base;
 
-    // B buffer of slice q in local chunk lc, and how many times that buffer
-    // was filled before
-    auto bbuf = [](int q, int lc) { return q == 1 ? ((lc & 1) ? S : 0) : q - 1; };
-    auto buse = [](int q, int lc) { return q == 1 ? (lc >> 1) : lc; };
+    // B buffer of slice q in chunk gc of this CTA, and how many times that
+    // buffer was filled before
+    auto bbuf = [](int q, int gc) { return q == 1 ? ((gc & 1) ? S : 0) : q - 1; };
+    auto buse = [](int q, int gc) { return q == 1 ? (gc >> 1) : gc; };
+    // unit -> column tile, row tile, K range
+    auto unit = [&](int u, int &j0, int64_t &i0, int &z, int &c0, int &c1) {
+        const int x = u % args.tx, y = (u / args.tx) % args.ty;
+        z = u / (args.tx * args.ty);
+        j0 = x * kW;
+        i0 = (int64_t)y * kBM;
+        c0 = z * args.csplit;
+        c1 = min(nch, c0 + args.csplit);
+    };
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -341,27 +352,32 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             tc::prefetch_tmap(&tmB);
             constexpr ProducerOrder<S> order;
             bool ok = true;
-            for (int c = c0; c < c1 && ok; c++) {
-                const int lc = c - c0;
+            int gc = 0;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                int j0, z, c0, c1;
+                int64_t i0;
+                unit(u, j0, i0, z, c0, c1);
+                for (int c = c0; c < c1 && ok; c++, gc++) {
 #pragma unroll
-                for (int it = 0; it < 3 * S; it++) {
-                    if (order.kind[it] == 0) {
-                        const int pi = order.idx[it];
-                        const int u = S2 * lc + pi, st = u % kAStages, n = u / kAStages;
-                        if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                        tc::mbar_expect_tx(&fullA[st], kATile);
-                        // part (slice p, re/im) = pi in the A tensor's part order
-                        tc::tma_load_3d(sA + st * kATile, &tmA, 0, (int)i0, pi * nch + c, &fullA[st]);
-                    } else {
-                        const int q = order.idx[it];
-                        const int b = bbuf(q, lc), n = buse(q, lc);
-                        if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                        tc::mbar_expect_tx(&fullB[b], kBSlice);
-                        uint8_t *bdst = sB + b * kBSlice;
-                        // smem [-Yi | Yr | Yi] from parts 2, 0, 1
-                        tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, &fullB[b]);
-                        tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, &fullB[b]);
-                        tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, &fullB[b]);
+                    for (int it = 0; it < 3 * S; it++) {
+                        if (order.kind[it] == 0) {
+                            const int pi = order.idx[it];
+                            const int ua = S2 * gc + pi, st = ua % kAStages, n = ua / kAStages;
+                            if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                            tc::mbar_expect_tx(&fullA[st], kATile);
+                            // part (slice p, re/im) = pi in the A tensor's part order
+                            tc::tma_load_3d(sA + st * kATile, &tmA, 0, (int)i0, pi * nch + c, &fullA[st]);
+                        } else {
+                            const int q = order.idx[it];
+                            const int b = bbuf(q, gc), n = buse(q, gc);
+                            if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                            tc::mbar_expect_tx(&fullB[b], kBSlice);
+                            uint8_t *bdst = sB + b * kBSlice;
+                            // smem [-Yi | Yr | Yi] from parts 2, 0, 1
+                            tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, &fullB[b]);
+                            tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, &fullB[b]);
+                            tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, &fullB[b]);
+                        }
                     }
                 }
             }
@@ -371,64 +387,73 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
             bool ok = true;
-            for (int c = c0; c < c1 && ok; c++) {
-                const int lc = c - c0;
+            int gc = 0, uc = 0;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
+                int j0, z, c0, c1;
+                int64_t i0;
+                unit(u, j0, i0, z, c0, c1);
+                for (int c = c0; c < c1 && ok; c++, gc++) {
+                    const bool first = (c == c0);
 #pragma unroll
-                for (int pi = 0; pi < S2; pi++) {
-                    const int p = pi / 2 + 1, ri = pi & 1;
-                    const int u = S2 * lc + pi, st = u % kAStages;
-                    if (!tc::mbar_wait(&fullA[st], (u / kAStages) & 1, &abort_flag)) { ok = false; break; }
-                    tc::fence_after();
-                    const uint64_t a0 = tc::sdesc_sw128(sA + st * kATile);
-                    // kk outer, q inner: the MMAs of one K step share their A
-                    // tile, read from shared memory once into the collector
-                    // buffer and reused for every slice q of Y
+                    for (int pi = 0; pi < S2; pi++) {
+                        const int p = pi / 2 + 1, ri = pi & 1;
+                        const int ua = S2 * gc + pi, st = ua % kAStages;
+                        if (!tc::mbar_wait(&fullA[st], (ua / kAStages) & 1, &abort_flag)) { ok = false; break; }
+                        tc::fence_after();
+                        const uint64_t a0 = tc::sdesc_sw128(sA + st * kATile);
+                        // kk outer, q inner: the MMAs of one K step share their A
+                        // tile, read from shared memory once into the collector
+                        // buffer and reused for every slice q of Y
 #pragma unroll
-                    for (int kk = 0; kk < kKC / 16; kk++) {
+                        for (int kk = 0; kk < kKC / 16; kk++) {
 #pragma unroll
-                        for (int q = S + 1 - p; q >= 1; q--) {
-                            const int g = p + q;
-                            const int b = bbuf(q, lc);
-                            if (pi == 0 && kk == 0) {
-                                if (!tc::mbar_wait(&fullB[b], buse(q, lc) & 1, &abort_flag)) { ok = false; break; }
-                                if (g <= kEx && lc >= 1 &&
-                                    !tc::mbar_wait(&accEmpty[g - 2], (lc - 1) & 1, &abort_flag)) { ok = false; break; }
-                                tc::fence_after();
+                            for (int q = S + 1 - p; q >= 1; q--) {
+                                const int g = p + q;
+                                const int b = bbuf(q, gc);
+                                if (pi == 0 && kk == 0) {
+                                    if (!tc::mbar_wait(&fullB[b], buse(q, gc) & 1, &abort_flag)) { ok = false; break; }
+                                    if (g <= kEx && gc >= 1 &&
+                                        !tc::mbar_wait(&accEmpty[g - 2], (gc - 1) & 1, &abort_flag)) { ok = false; break; }
+                                    // the tail of the previous unit must have been read
+                                    if (g > kEx && first && q == S && uc >= 1 &&
+                                        !tc::mbar_wait(&tailEmpty, (uc - 1) & 1, &abort_flag)) { ok = false; break; }
+                                    tc::fence_after();
+                                }
+                                const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
+                                const uint8_t *bq = sB + b * kBSlice;
+                                // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
+                                const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
+                                // a fresh sum: every exact diagonal at its first pair
+                                // of the chunk, the tail at its first pair of the unit
+                                const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
+                                                              : (first && pi == 0 && q == S);
+                                const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
+                                const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
+                                // no collector in the chunk's first pass, whose MMAs
+                                // wait on barriers between them, nor for a single pair
+                                if (pi == 0 || p == S)
+                                    tc::mma_bf16(d, a, bd, idesc, acc);
+                                else if (q == S + 1 - p)
+                                    tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                                else if (q == 1)
+                                    tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                                else
+                                    tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
                             }
-                            const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
-                            const uint8_t *bq = sB + b * kBSlice;
-                            // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
-                            const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
-                            // a fresh sum: every exact diagonal at its first pair
-                            // of the chunk, the tail at its first pair of the CTA
-                            const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
-                                                          : (lc == 0 && pi == 0 && q == S);
-                            const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
-                            const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
-                            // no collector in the chunk's first pass, whose MMAs
-                            // wait on barriers between them, nor for a single pair
-                            if (pi == 0 || p == S)
-                                tc::mma_bf16(d, a, bd, idesc, acc);
-                            else if (q == S + 1 - p)
-                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
-                            else if (q == 1)
-                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
-                            else
-                                tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
+                            if (!ok) break;
                         }
                         if (!ok) break;
-                    }
-                    if (!ok) break;
-                    tc::mma_commit(&emptyA[st]);
-                    if (ri == 1) {
-                        // last reader of B slice S + 1 - p; last pair of diagonal p + 1
-                        const int qd = S + 1 - p;
-                        tc::mma_commit(&emptyB[bbuf(qd, lc)]);
-                        if (p + 1 <= kEx) tc::mma_commit(&accFull[p - 1]);
+                        tc::mma_commit(&emptyA[st]);
+                        if (ri == 1) {
+                            // last reader of B slice S + 1 - p; last pair of diagonal p + 1
+                            const int qd = S + 1 - p;
+                            tc::mma_commit(&emptyB[bbuf(qd, gc)]);
+                            if (p + 1 <= kEx) tc::mma_commit(&accFull[p - 1]);
+                        }
                     }
                 }
+                if (ok && kTail) tc::mma_commit(&tailFull);
             }
-            if (ok && kTail) tc::mma_commit(&tailFull);
         }
     } else {
         // ------------------------------------------------ drain + epilogue
@@ -437,86 +462,95 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int quad = warp & 3, half = (warp - 2) >> 2;
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
-        long long Sx[kHalf];
-#pragma unroll
-        for (int j = 0; j < kHalf; j++) Sx[j] = 0;
         bool ok = true;
-        for (int c = c0; c < c1 && ok; c++) {
-            const int lc = c - c0;
+        int gc = 0, uc = 0;
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
+            int j0, z, c0, c1;
+            int64_t i0;
+            unit(u, j0, i0, z, c0, c1);
+            long long Sx[kHalf];
 #pragma unroll
-            for (int g = 2; g <= kEx; g++) {
-                if (!tc::mbar_wait(&accFull[g - 2], lc & 1, &abort_flag)) { ok = false; break; }
-                tc::fence_after();
-                const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
-                uint32_t r[kHalf];
+            for (int j = 0; j < kHalf; j++) Sx[j] = 0;
+            for (int c = c0; c < c1 && ok; c++, gc++) {
 #pragma unroll
-                for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, r + h);
-                tc::tmem_wait_ld();
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&accEmpty[g - 2]);
-                const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
-                const int shift = kBeta * (5 - g);                             // S in units of 2^-40
+                for (int g = 2; g <= kEx; g++) {
+                    if (!tc::mbar_wait(&accFull[g - 2], gc & 1, &abort_flag)) { ok = false; break; }
+                    tc::fence_after();
+                    const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
+                    const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
+                    const int shift = kBeta * (5 - g);                             // S in units of 2^-40
+                    // 16 columns at a time (registers are the limit here)
 #pragma unroll
-                for (int u = 0; u < kHalf; u++) {
-                    const int dv = __float2int_rn(__uint_as_float(r[u]) * scale);
-                    Sx[u] += (long long)dv << shift;
-                }
-            }
-        }
-        float T[kHalf];
+                    for (int h = 0; h < kHalf; h += 16) {
+                        uint32_t r[16];
+                        tc::tmem_ld16(tmem + lane_addr + col + h, r);
+                        tc::tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < kHalf; j++) T[j] = 0.f;
-        if (ok && kTail) {
-            if (tc::mbar_wait(&tailFull, 0, &abort_flag)) {
-                tc::fence_after();
-                const uint32_t col = (uint32_t)(kNEx * kN + half * kHalf);
-                uint32_t r[kHalf];
-#pragma unroll
-                for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, r + h);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int u = 0; u < kHalf; u++) T[u] = __uint_as_float(r[u]);
-            } else {
-                ok = false;
-            }
-        }
-        if (ok) {
-            const int64_t i = i0 + row;
-            if (i < args.M) {
-                int e = args.E[i];
-                if (e == INT_MIN) e = 0;
-#pragma unroll
-                for (int u = 0; u < kHalf; u++) {
-                    const int j = j0 + u;
-                    if (j >= args.n) continue;
-                    int f = args.F[j];
-                    if (f == INT_MIN) f = 0;
-                    const double v = ldexp((double)Sx[u] * 0x1.0p-40 + (double)T[u], e + f);
-                    double out = v;
-                    if (args.P) {        // split-K partial; summed and finished by k_split_reduce
-                        double *pp = (double *)(args.P + ((int64_t)blockIdx.z * args.n + j) * args.M + i);
-                        pp[half] = out;
-                        continue;
-                    }
-                    if (args.ep.mode == GEMM_CHEB) {
-                        const double y = half ? args.Y[i + j * args.ldy].y : args.Y[i + j * args.ldy].x;
-                        out = args.ep.s1 * (v - args.ep.c * y);
-                        if (args.ep.Yp) {
-                            const z_t yp = args.ep.Yp[i + j * args.ep.ldyp];
-                            out -= args.ep.s2 * (half ? yp.y : yp.x);
+                        for (int v = 0; v < 16; v++) {
+                            const int dv = __float2int_rn(__uint_as_float(r[v]) * scale);
+                            Sx[h + v] += (long long)dv << shift;
                         }
                     }
-                    double *cp = (double *)(args.C + i + j * args.ldc);
-                    cp[half] = out;
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&accEmpty[g - 2]);
                 }
+            }
+            uint32_t T[kHalf];           // FP32 bits of the tail
+#pragma unroll
+            for (int j = 0; j < kHalf; j++) T[j] = 0u;
+            if (ok && kTail) {
+                if (tc::mbar_wait(&tailFull, uc & 1, &abort_flag)) {
+                    tc::fence_after();
+                    const uint32_t col = (uint32_t)(kNEx * kN + half * kHalf);
+#pragma unroll
+                    for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, T + h);
+                    tc::tmem_wait_ld();
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&tailEmpty);
+                } else {
+                    ok = false;
+                }
+            }
+            if (!ok) break;
+            // Recombination C = 2^(e+f) (S 2^-40 + T) into the FP64 partial
+            // of this split (k_split_reduce sums the splits and applies the
+            // epilogue).  The column exponents of the tile come from two
+            // coalesced loads per warp and warp shuffles: one dependent
+            // global load per column, issued behind the previous column's
+            // store, cost about a microsecond each under this kernel's HBM
+            // traffic.  FP64 issue is slow on this part, so the powers of two
+            // are built from exponent bits.
+            const int jn = args.n - j0;                      // valid columns of the tile
+            const int fa = (lane < jn) ? args.F[j0 + lane] : 0;
+            const int fb = (lane + 32 < kW && lane + 32 < jn) ? args.F[j0 + 32 + lane] : 0;
+            const int64_t i = i0 + row;
+            int e = (i < args.M) ? args.E[i] : 0;
+            if (e == INT_MIN) e = 0;
+            double *pbase = (double *)(args.P + ((int64_t)z * args.n + j0) * args.M + i) + half;
+#pragma unroll
+            for (int v = 0; v < kHalf; v++) {
+                int f = (v < 32) ? __shfl_sync(0xffffffffu, fa, v) : __shfl_sync(0xffffffffu, fb, v - 32);
+                if (v >= jn) continue;
+                if (f == INT_MIN) f = 0;
+                const int x = e + f;
+                double val;
+                if (x > -960 && x < 1000) {
+                    const double sc = __longlong_as_double((long long)(1023 + x) << 52);
+                    const double sc40 = __longlong_as_double((long long)(1023 - 40 + x) << 52);
+                    val = fma((double)Sx[v], sc40, (double)__uint_as_float(T[v]) * sc);
+                } else {
+                    val = ldexp((double)Sx[v] * 0x1.0p-40 + (double)__uint_as_float(T[v]), x);
+                }
+                if (i < args.M) pbase[(int64_t)v * args.M * 2] = val;
             }
         }
     }
 
     tc::fence_before();
     __syncthreads();
-    if (abort_flag && threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.y * gridDim.x + blockIdx.x);
+    if (abort_flag && threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.x);
     if (warp == 1) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, kTmemCols);
@@ -578,6 +612,11 @@ int64_t ozaki_padded(int64_t N) { return (N + 127) / 128 * 128; }
 size_t ozaki_a_bytes(int64_t N) {
     const int64_t Np = ozaki_padded(N);
     return (size_t)kS * 2 * Np * Np * 2;
+}
+
+size_t ozaki_partial_bytes(int64_t N, int m) {
+    const int mp = (m + kW - 1) / kW * kW;
+    return (size_t)N * sizeof(z_t) * std::max<int64_t>(16 * kW, 8 * (int64_t)mp);
 }
 
 size_t ozaki_b_bytes(int64_t N, int m) {
@@ -646,34 +685,43 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.nchunks = (int)(Np / kKC);
     a.E = oh.E;
     a.F = F;
-    a.ep = ep;
-    a.Y = Y;
-    a.ldy = ldy;
-    a.C = C;
-    a.ldc = ldc;
     a.sc = sc;
-    // split K so that the CTAs fill whole waves of the SMs: the smallest
-    // ceil(tiles * s / sms) / s over s, with at least 16 K chunks per split
-    // and the partials bounded by the workspace
-    const int tiles = (mp / kW) * (int)(Np / kBM);
+    // Split K into `sp` ranges so that the units (tiles x splits) spread
+    // evenly over one persistent CTA per SM.  Cost in K-chunk units: the
+    // busiest CTA's units, each with half a chunk of pipeline fill and
+    // drain, plus the FP64 partials written and summed by k_split_reduce
+    // (32 bytes per complex output and split, at about one chunk per 6 us
+    // and 6 TB/s).
+    // At least 16 K chunks per split, partials within the workspace.
+    const int tx = mp / kW, ty = (int)(Np / kBM);
+    const int tiles = tx * ty;
     int best = 1;
     double best_t = 1e30;
-    for (int sp = 1; sp <= 16; sp++) {
+    if ((int64_t)n * N * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) return cudaErrorInvalidValue;
+    for (int sp = 1; sp <= 32; sp++) {
         if ((int64_t)sp * 16 > a.nchunks && sp > 1) break;
-        if ((int64_t)sp * n * N * (int64_t)sizeof(z_t) > partial_bytes && sp > 1) break;
-        const double t = (double)((tiles * sp + sms - 1) / sms) / sp * (1.0 + 0.01 * (sp - 1));
-        if (t < best_t - 1e-12) { best_t = t; best = sp; }
+        if ((int64_t)sp * n * N * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) break;
+        const int64_t u = (int64_t)tiles * sp;
+        const int64_t per = (u + sms - 1) / sms;
+        const double chunks = (double)((a.nchunks + sp - 1) / sp);
+        const double part = (double)sp * n * N * 32.0 / (6.0e12 * 6.0e-6);
+        const double t = (double)per * (chunks + 0.5) + part;
+        if (t < best_t - 1e-9) { best_t = t; best = sp; }
     }
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
-    a.P = (nsplit > 1) ? partials : nullptr;
-    dim3 grid((unsigned)(mp / kW), (unsigned)(Np / kBM), (unsigned)nsplit);
+    a.P = partials;
+    a.tx = tx;
+    a.ty = ty;
+    a.tz = nsplit;
+    const int64_t units = (int64_t)tiles * nsplit;
+    dim3 grid((unsigned)std::min<int64_t>(units, sms));
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
     if (ev0) cudaEventRecord(ev0, st);
     cudaError_t e = low ? launch_variant<CfgMixed>(tmA, tmB, a, grid, st)
                         : launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
     if (ev1) cudaEventRecord(ev1, st);
-    if (e != cudaSuccess || nsplit == 1) return e;
+    if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
     k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, partials, ep, Y, ldy, C, ldc);
     bse_count_launches(1);

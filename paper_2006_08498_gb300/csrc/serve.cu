@@ -85,6 +85,7 @@ size_t estimate_run_bytes(int64_t N, int m, int nev, int precision) {
     if (precision != CHASE_FP64_DFMA) {
         b += 24 * Np * Np;                                  // slices of H
         b += 36 * mp * Np;                                  // slices of the operand
+        b += ozaki_partial_bytes(N, std::max(m, 32));       // split-K partials
     }
     return b;
 }
