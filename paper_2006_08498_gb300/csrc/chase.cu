@@ -334,8 +334,9 @@ int cholqr_pass(bsechase_ctx *ctx, z_t *V, int64_t ldv, int64_t N, int m, double
     CK(launch_zgemm_cn(m, m, N, V, ldv, V, ldv, G, m, shift, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
     CK(launch_cholesky(m, G, m, ctx->sc, ctx->st));
     CK(launch_trinv(m, G, m, Ri, m, ctx->st));
-    GemmEpi plain{};
-    CK(launch_zgemm_nn(N, m, m, V, ldv, Ri, m, B1, N, plain, ctx->st));
+    GemmEpi tri{};
+    tri.b_upper = 1;              // R^{-1} is upper triangular
+    CK(launch_zgemm_nn(N, m, m, V, ldv, Ri, m, B1, N, tri, ctx->st));
     CK(launch_copy_cols(N, m, B1, N, V, ldv, nullptr, ctx->st));
     return BSE_OK;
 }

@@ -24,6 +24,7 @@ struct GemmEpi {
     int64_t ldyp;
     const z_t *D;          // SUB: C = D - AB (may alias C)
     int64_t ldd;
+    int b_upper;           // B is upper triangular: B[k, j] = 0 for k > j (skipped)
 };
 // C[M x n] = epi(A[M x K] B[K x n]), all column-major FP64 complex.
 cudaError_t launch_zgemm_nn(int64_t M, int64_t n, int64_t K, const z_t *A, int64_t lda,

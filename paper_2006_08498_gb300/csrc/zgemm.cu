@@ -42,7 +42,9 @@ zgemm_nn_kernel(int64_t M, int64_t n, int64_t K, const z_t *__restrict__ A, int6
 #pragma unroll
         for (int b = 0; b < TN; b++) acc[a][b] = zmk(0.0, 0.0);
 
-    for (int64_t k0 = 0; k0 < K; k0 += kBK) {
+    // an upper triangular B has no rows below this tile's last column
+    const int64_t Ke = (ep.b_upper && j0 + BN < K) ? j0 + BN : K;
+    for (int64_t k0 = 0; k0 < Ke; k0 += kBK) {
         // A tile: BM rows x kBK columns, rows contiguous in memory
         for (int e = tid; e < BM * kBK; e += kThreads) {
             const int r = e % BM, kk = e / BM;
@@ -108,9 +110,12 @@ constexpr int kGBK = 32;   // K step
 
 __global__ void __launch_bounds__(kThreads)
 zgemm_cn_partial(int64_t m1, int64_t m2, int64_t K, int64_t kchunk, const z_t *__restrict__ A,
-                 int64_t lda, const z_t *__restrict__ B, int64_t ldb, z_t *__restrict__ P) {
+                 int64_t lda, const z_t *__restrict__ B, int64_t ldb, z_t *__restrict__ P,
+                 int upper) {
     __shared__ z_t As[kGBK][kGT + 1];
     __shared__ z_t Bs[kGBK][kGT + 1];
+    // Hermitian product (A = B): tiles below the diagonal are mirrored
+    if (upper && blockIdx.y < blockIdx.x) return;
     const int tid = threadIdx.x;
     const int ti = tid % 16, tj = tid / 16;
     const int64_t i0 = (int64_t)blockIdx.x * kGT, j0 = (int64_t)blockIdx.y * kGT;
@@ -151,13 +156,24 @@ zgemm_cn_partial(int64_t m1, int64_t m2, int64_t K, int64_t kchunk, const z_t *_
 }
 
 // G = sum_z P[z] in increasing z, + shift on the diagonal; optionally
-// replaced by its Hermitian part (G + G^H)/2 (square G only).
+// replaced by its Hermitian part (G + G^H)/2 (square G only).  upper: only
+// the tiles on and above the diagonal were computed (A = B); the lower
+// triangle is the conjugate of the upper one.
 __global__ void zgemm_cn_reduce(int64_t m1, int64_t m2, int nsplit, const z_t *__restrict__ P,
-                                z_t *G, int64_t ldg, double shift, int hermitize) {
+                                z_t *G, int64_t ldg, double shift, int hermitize, int upper) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m1 * m2) return;
     const int64_t i = e % m1, j = e / m1;
     z_t s = zmk(0.0, 0.0), t = zmk(0.0, 0.0);
+    if (upper) {
+        const int64_t r = i <= j ? i : j, c = i <= j ? j : i;
+        for (int z = 0; z < nsplit; z++) s = zadd(s, P[(int64_t)z * m1 * m2 + r + c * m1]);
+        if (i > j) s.y = -s.y;
+        if (i == j) s.y = 0.0;
+        if (i == j) s.x += shift;
+        G[i + j * ldg] = s;
+        return;
+    }
     for (int z = 0; z < nsplit; z++) s = zadd(s, P[(int64_t)z * m1 * m2 + i + j * m1]);
     if (hermitize) {
         for (int z = 0; z < nsplit; z++) t = zadd(t, P[(int64_t)z * m1 * m2 + j + i * m1]);
@@ -168,8 +184,9 @@ __global__ void zgemm_cn_reduce(int64_t m1, int64_t m2, int nsplit, const z_t *_
     G[i + j * ldg] = s;
 }
 
-int cn_nsplit(int64_t m1, int64_t m2, int64_t K) {
-    const int64_t tiles = ((m1 + kGT - 1) / kGT) * ((m2 + kGT - 1) / kGT);
+int cn_nsplit(int64_t m1, int64_t m2, int64_t K, bool upper = false) {
+    const int64_t t1 = (m1 + kGT - 1) / kGT, t2 = (m2 + kGT - 1) / kGT;
+    const int64_t tiles = upper ? t1 * (t1 + 1) / 2 : t1 * t2;
     int64_t ns = (4 * 152 + tiles - 1) / tiles;           // ~4 CTAs per SM
     const int64_t maxs = (K + 255) / 256;                   // >= 256 rows per split
     if (ns > maxs) ns = maxs;
@@ -202,16 +219,18 @@ cudaError_t launch_zgemm_cn(int64_t m1, int64_t m2, int64_t K, const z_t *A, int
                             const z_t *B, int64_t ldb, z_t *G, int64_t ldg, double shift,
                             int hermitize, z_t *work, int64_t work_elems, cudaStream_t st) {
     if (m1 <= 0 || m2 <= 0) return cudaSuccess;
-    int ns = cn_nsplit(m1, m2, K);
+    // A^H A is Hermitian: compute the upper tiles only
+    const int upper = (A == B && lda == ldb && m1 == m2) ? 1 : 0;
+    int ns = cn_nsplit(m1, m2, K, upper != 0);
     if ((int64_t)ns * m1 * m2 > work_elems) ns = (int)(work_elems / (m1 * m2));
     if (ns < 1) return cudaErrorInvalidValue;
     const int64_t kchunk = (((K + ns - 1) / ns) + kGBK - 1) / kGBK * kGBK;
     dim3 grid((unsigned)((m1 + kGT - 1) / kGT), (unsigned)((m2 + kGT - 1) / kGT), (unsigned)ns);
-    zgemm_cn_partial<<<grid, kThreads, 0, st>>>(m1, m2, K, kchunk, A, lda, B, ldb, work);
+    zgemm_cn_partial<<<grid, kThreads, 0, st>>>(m1, m2, K, kchunk, A, lda, B, ldb, work, upper);
     bse_count_launches(1);
     const int64_t tot = m1 * m2;
     zgemm_cn_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m1, m2, ns, work, G, ldg, shift,
-                                                                  hermitize);
+                                                                  hermitize, upper);
     bse_count_launches(1);
     return cudaGetLastError();
 }
