@@ -4,7 +4,9 @@ One step = the whole hot path on one synthetic BSE Hamiltonian: generate
 H on the device (Eq. (1) stand-in), then solve for the lowest nev
 eigenpairs (Lanczos, filter, QR, Rayleigh-Ritz, residuals/locking, output).
 Workload: N = 20000 (Nk = 1250, Nv = Nc = 4), nev = 100, nex = 40,
-deg_max = 36, tol = 1e-10, complex FP64.  H is 6.4 GB, far larger than L2,
+deg_max = 36, tol = 1e-10, complex FP64.  The filter degrees of Eq. (S1) are
+raised in groups of 48 columns, the tile width of the tensor-core product
+(--degree-group; 0 keeps them unchanged).  H is 6.4 GB, far larger than L2,
 so no L2 flush is needed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -248,7 +250,7 @@ def run_ours(args, rank, world, local_rank):
     def step():
         ctx.build_hamiltonian(W["seed"] + rank, W["Nk"], W["Nv"], W["Nc"], out=H)
         return ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs,
-                         precision=prec)
+                         precision=prec, degree_group=args.degree_group)
 
     for _ in range(args.warmup):
         step()
@@ -286,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh,
-                           precision=prec)
+                           precision=prec, degree_group=args.degree_group)
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         if dist:
@@ -302,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
-            "config": dict(W, precision=args.precision,
+            "config": dict(W, precision=args.precision, degree_group=args.degree_group,
                            parallelism="replicas" if world > 1 else "single"),
             "throughput_solves_per_s": world * args.steps / (ms_max / 1e3),
             "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs",
@@ -421,6 +423,9 @@ def main():
     ap.add_argument("--nk", type=int, default=WORKLOAD["Nk"], help="k-points (N = 16 Nk)")
     ap.add_argument("--nev", type=int, default=WORKLOAD["nev"])
     ap.add_argument("--nex", type=int, default=WORKLOAD["nex"])
+    ap.add_argument("--degree-group", type=int, default=48,
+                    help="48 (default): filter degrees raised in groups of one tensor-core "
+                         "tile; 0: the per-vector degrees of Eq. (S1) unchanged")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

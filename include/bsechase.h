@@ -91,6 +91,15 @@ typedef struct {
     const void *d_V0;    /* optional warm start: N x n_v0 device block        */
     int64_t ldv0;
     int n_v0;            /* 0 = none; at most nev + nex columns are used      */
+    int degree_group;    /* 0 (default): the per-vector degrees of Eq. (S1).
+                            > 0: before each filter the degrees (ascending) are
+                            taken in groups of this many columns from the
+                            highest down and raised to the group's largest.
+                            A filter product costs the same for any column
+                            count within one tile of the tensor-core kernel
+                            (48 columns), so 48 filters some columns further
+                            at no cost; never lowers a degree.  No counterpart
+                            in the paper. */
 } chase_opts;
 
 /* Per-solve statistics (times in milliseconds, CUDA events on the stream). */

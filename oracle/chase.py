@@ -377,14 +377,35 @@ def normalize_phase(V):
 
 # -------------------------------------------------------------- the solve
 
+def group_degrees(deg, width):
+    """Degrees in groups of `width`: with the degrees ascending, the columns
+    are taken in groups of `width` from the highest degree down, and every
+    degree of a group is raised to the group's largest.  A filter step costs
+    the same for any number of columns within one group, so this adds
+    filtering (never removes it) at no cost on such hardware.  width <= 0:
+    unchanged."""
+    deg = np.array(deg, dtype=np.int64, copy=True)
+    if width <= 0:
+        return deg
+    hi = len(deg)
+    while hi > 0:
+        lo = max(0, hi - width)
+        deg[lo:hi] = deg[hi - 1]
+        hi = lo
+    return deg
+
+
 def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
-          seed=0, V0=None, lanczos_runs=4, lanczos_steps=25, trace=False):
+          seed=0, V0=None, lanczos_runs=4, lanczos_steps=25, trace=False,
+          degree_group=0):
     """Lowest nev eigenpairs of the Hermitian H by ChASE.
 
     Lanczos estimate, then per iteration: interval (c, e) from (alpha,
     beta); filter the unlocked columns with their degrees; QR; Rayleigh-
     Ritz; residuals; lock; alpha <- largest Ritz value, lower <- min(lower,
     smallest Ritz value); new degrees; unlocked columns sorted by degree.
+    degree_group > 0 raises the degrees in groups (group_degrees) before
+    each filter; 0 keeps the degrees of Eq. (S1).
     Returns a dict with ascending eigenvalues, eigenvectors (phase-
     normalised), residuals, iteration and matvec counts, and a status
     ("ok" or "noconv")."""
@@ -414,6 +435,7 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
         cap = degree_cap(lower, c, e)
         if cap is not None:
             deg = np.minimum(deg, cap)
+        deg = group_degrees(deg, degree_group)
         Vf, mv = chebyshev_filter(H, V[:, locked:], deg, lower, c, e)
         matvecs += mv
         Q = qr(V[:, :locked], Vf)

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("deg_init", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("lanczos_vecs", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("d_V0", ctypes.c_void_p),
-                ("ldv0", ctypes.c_int64), ("n_v0", ctypes.c_int)]
+                ("ldv0", ctypes.c_int64), ("n_v0", ctypes.c_int),
+                ("degree_group", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -273,8 +274,8 @@ class Context:
 
     # -------------------------------------------------------------- solve
     @staticmethod
-    def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0):
-        o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0)
+    def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group=0):
+        o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0, degree_group)
         if V0 is not None:
             o.d_V0 = ctypes.c_void_p(V0.data_ptr())
             o.ldv0 = _ld(V0)
@@ -283,7 +284,7 @@ class Context:
 
     def solve(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64, deg_init=20,
               max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0, V0=None,
-              evecs=None, allow_noconv=False):
+              evecs=None, allow_noconv=False, degree_group=0):
         """Lowest nev eigenpairs of the device Hermitian H (column-major).
         Returns (evals ndarray, evecs tensor N x nev, resid ndarray, stats)."""
         N = H.shape[0]
@@ -292,7 +293,7 @@ class Context:
         if evecs is None:
             evecs = colmajor_empty(N, nev, device=H.device)
         st = Stats()
-        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0)
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group)
         rc = load().chase_solve(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), nev, nex,
                                 tol, deg_max, precision, ctypes.byref(o), _dp(evals),
                                 ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
@@ -304,7 +305,7 @@ class Context:
 
     def solve_host(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
                    deg_init=20, max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0,
-                   evecs=None):
+                   evecs=None, degree_group=0):
         """As solve(), with H and the eigenvectors in host memory (Fortran-
         ordered complex128 numpy arrays, ideally pinned)."""
         N = H.shape[0]
@@ -313,7 +314,7 @@ class Context:
         if evecs is None:
             evecs = np.zeros((N, nev), dtype=np.complex128, order="F")
         st = Stats()
-        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None)
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, degree_group)
         hp = H.data_ptr() if hasattr(H, "data_ptr") else H.ctypes.data
         ep = evecs.data_ptr() if hasattr(evecs, "data_ptr") else evecs.ctypes.data
         rc = load().chase_solve_host(self._h, ctypes.c_void_p(hp), N, _ld(H), nev, nex, tol,

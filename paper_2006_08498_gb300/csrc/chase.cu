@@ -421,8 +421,10 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         o.d_V0 = opts->d_V0;
         o.ldv0 = opts->ldv0;
         o.n_v0 = opts->n_v0;
+        o.degree_group = opts->degree_group;
     }
     if (o.d_V0 && (o.n_v0 < 0 || o.ldv0 < N)) return fail(ctx, BSE_EINVAL, "bad warm-start block%s");
+    if (o.degree_group < 0) return fail(ctx, BSE_EINVAL, "degree_group must be >= 0%s");
     if ((rc = ensure_workspace(ctx, N, m))) return rc;
     Small s = small_layout(ctx, m);
     z_t *V = (z_t *)ctx->V.p, *B2 = (z_t *)ctx->B2.p, *B3 = (z_t *)ctx->B3.p;
@@ -468,6 +470,17 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
             cap -= cap & 1;
             if (cap < 2) cap = 2;
             for (int j = 0; j < ma; j++) hdeg[j] = std::min(hdeg[j], cap);
+        }
+        // optional degree groups: with the degrees ascending, groups of
+        // o.degree_group columns from the highest down take the group's
+        // largest degree (a filter step costs the same for any column count
+        // within one tile of the product kernel)
+        if (o.degree_group > 0) {
+            for (int hi = ma; hi > 0;) {
+                const int lo = std::max(0, hi - o.degree_group);
+                for (int j = lo; j < hi; j++) hdeg[j] = hdeg[hi - 1];
+                hi = lo;
+            }
         }
         CK(cudaMemcpyAsync(s.deg, hdeg.data(), ma * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
         tm.mark(2);

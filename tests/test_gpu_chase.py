@@ -434,3 +434,18 @@ def test_solve_full_size_certified(ctx):
     assert np.linalg.norm(V.conj().T @ V - np.eye(nev)) <= 1e-11
     assert np.all(np.diff(evals) >= 0)
     assert 2 <= st["iters"] <= 20
+
+
+def test_solve_grouped_degrees_matches_oracle(ctx, c1):
+    """degree_group = 48: the same eigenpairs as the oracle's ChASE with the
+    same grouping (and as the dense oracle), iterations within one."""
+    H, w, _ = c1
+    ref = oracle.chase(H, 50, 25, tol=1e-10, deg_max=36, degree_group=48)
+    Hd = ctx.build_hamiltonian(0, 125, 4, 4)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, degree_group=48)
+    _check_solution(H, evals, host(Vd), resid, 50, w_exact=w, ref=ref["evecs"])
+    assert np.max(resid) <= 1e-10
+    assert np.allclose(evals, ref["evals"], rtol=1e-12, atol=0)
+    assert abs(st["iters"] - ref["iters"]) <= 1
+    with pytest.raises(pkg.BseError):
+        ctx.solve(Hd, 50, 25, degree_group=-1)

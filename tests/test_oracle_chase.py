@@ -218,3 +218,36 @@ def test_chase_full_search_space():
     r = oracle.chase(H, 40, 8)
     assert r["status"] == "ok"
     assert np.max(np.abs(r["evals"] - w[:40])) < 1e-12
+
+
+@pytest.mark.parametrize("width", [0, 1, 4, 48])
+def test_group_degrees_properties(width):
+    rng = np.random.default_rng(width + 3)
+    deg = np.sort(rng.integers(1, 19, size=75) * 2)
+    g = oracle.group_degrees(deg, width)
+    assert np.all(np.diff(g) >= 0) and np.all(g >= deg)
+    if width <= 1:
+        assert np.array_equal(g, deg)
+        return
+    # groups of `width` from the top share the group's largest degree
+    hi = len(deg)
+    while hi > 0:
+        lo = max(0, hi - width)
+        assert np.all(g[lo:hi] == deg[hi - 1])
+        hi = lo
+    # every filter step's active set is a union of whole groups from the top
+    allowed = {min(k * width, len(g)) for k in range(len(g) // width + 2)}
+    for t in range(1, int(g.max()) + 1):
+        assert int(np.sum(g >= t)) in allowed
+
+
+def test_chase_grouped_degrees_matches_dense():
+    """Grouped degrees only add filtering: the solve reaches the same
+    eigenpairs as the dense eigensolver, in no more iterations."""
+    H = oracle.build_h(0, 30, 4, 4)
+    w, _ = oracle.eigh(H, 41)
+    plain = oracle.chase(H, 40, 16)
+    r = oracle.chase(H, 40, 16, degree_group=48)
+    assert r["status"] == "ok" and r["iters"] <= plain["iters"]
+    assert np.max(np.abs(r["evals"] - w[:40]) / np.abs(w[:40])) < 1e-10
+    assert np.max(r["resid"]) <= 1e-10
