@@ -368,7 +368,8 @@ def run_serving(args):
     def submit(q, tickets):
         warm = tickets.get(q["warm"], 0) if q["warm"] is not None else 0
         return ctx.submit(q["seed"], q["Nk"], 4, 4, q["nev"], q["nex"], tol=1e-10, deg_max=36,
-                          precision=prec, model=dict(w0=q["w0"]), warm_ticket=warm)
+                          precision=prec, model=dict(w0=q["w0"]), warm_ticket=warm,
+                          degree_group=args.degree_group)
 
     # calibration: a back-to-back batch of the first 16 (cold) requests
     t0 = time.perf_counter()
@@ -402,7 +403,7 @@ def run_serving(args):
             "solves_per_s": n_req / (end - start), "requests": n_req, "ok": ok,
             "warm_requests": warm_used, "arrival_rate_per_s": rate,
             "calibrated_capacity_per_s": cap, "slots": args.slots, "budget_bytes": budget,
-            "precision": args.precision, "data": "synthetic",
+            "precision": args.precision, "degree_group": args.degree_group, "data": "synthetic",
             "config": {"workload": "serving_mix_256", "N": "16*U{63..1000}", "nev": "U{10..100}",
                        "nex": "max(10, ceil(nev/2))", "warm_fraction": 0.3, "tol": 1e-10}}
     print(json.dumps(line), flush=True)

@@ -254,6 +254,7 @@ typedef struct {
     int deg_max, precision;
     uint64_t warm_ticket;    /* 0, or a ticket whose eigenvectors (same N) start
                                 this solve if that request has finished       */
+    int degree_group;        /* as chase_opts.degree_group (0: Eq. (S1))       */
 } chase_request;
 
 typedef struct {

@@ -74,7 +74,7 @@ class Request(ctypes.Structure):
                 ("Nc", ctypes.c_int), ("use_model", ctypes.c_int), ("model", Model),
                 ("nev", ctypes.c_int), ("nex", ctypes.c_int), ("tol", ctypes.c_double),
                 ("deg_max", ctypes.c_int), ("precision", ctypes.c_int),
-                ("warm_ticket", ctypes.c_uint64)]
+                ("warm_ticket", ctypes.c_uint64), ("degree_group", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -382,7 +382,7 @@ class Context:
         self._check(load().chase_server_destroy(self._h))
 
     def submit(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
-               model=None, warm_ticket=0):
+               model=None, warm_ticket=0, degree_group=0):
         """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc);
         returns its ticket."""
         md = dict(DEFAULT_MODEL)
@@ -391,7 +391,7 @@ class Context:
         r = Request(seed, Nk, Nv, Nc, 1 if model else 0,
                     Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
                           int(md["rank_x"])),
-                    nev, nex, tol, deg_max, precision, warm_ticket)
+                    nev, nex, tol, deg_max, precision, warm_ticket, degree_group)
         t = ctypes.c_uint64(0)
         self._check(load().chase_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value

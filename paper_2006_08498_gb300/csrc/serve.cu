@@ -158,6 +158,7 @@ void worker(BseServer *S, int slot) {
                                        rq.use_model ? &rq.model : nullptr, dH, N);
         chase_opts o{};
         o.seed = rq.seed;
+        o.degree_group = rq.degree_group;
         if (warm) {
             o.d_V0 = warm->d_evecs;
             o.ldv0 = N;
@@ -265,7 +266,7 @@ int chase_server_submit(bsechase_ctx *ctx, const chase_request *req, uint64_t *t
     const int64_t N = bse_dim(req->Nk, req->Nv, req->Nc);
     const int m = req->nev + req->nex;
     if (N < 1 || req->nev < 1 || req->nex < 0 || m > N || m > 512 || !(req->tol > 0) ||
-        req->deg_max < 2 ||
+        req->deg_max < 2 || req->degree_group < 0 ||
         (req->precision != CHASE_FP64 && req->precision != CHASE_MIXED_FP32 &&
          req->precision != CHASE_FP64_DFMA))
         return fail(ctx, BSE_EINVAL, "invalid request%s");

@@ -113,7 +113,7 @@ def test_timeout_cancel_and_bad_requests(ctx):
     assert r2["status"] == pkg.BSE_EINVAL and r2["evals"] is None
     assert ctx.wait(t1)["status"] == pkg.BSE_OK
     for bad in (dict(nev=0, nex=5), dict(nev=40, nex=600), dict(nev=10, nex=5, tol=-1.0),
-                dict(nev=10, nex=5, precision=9)):
+                dict(nev=10, nex=5, precision=9), dict(nev=10, nex=5, degree_group=-2)):
         kw = dict(seed=1, Nk=16, Nv=4, Nc=4)
         kw.update(bad)
         with pytest.raises(pkg.BseError) as ei:
