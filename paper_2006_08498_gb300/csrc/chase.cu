@@ -67,7 +67,7 @@ void release_workspace(bsechase_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
                       &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
                       &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
-                      &ctx->ozB, &ctx->ozF, &ctx->ozP};
+                      &ctx->ozB, &ctx->ozF, &ctx->ozP, &ctx->ozGA, &ctx->ozGE};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFreeAsync(b->p, ctx->st);
         b->p = nullptr;
@@ -192,6 +192,10 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     if ((rc = ensure(ctx, ctx->ozF, (size_t)(mc + 64) * sizeof(int)))) return rc;
     const size_t pbytes = ozaki_partial_bytes(op.N, mc);
     if ((rc = ensure(ctx, ctx->ozP, pbytes))) return rc;
+    // general products of QR and Rayleigh-Ritz: op(A) is m x N (A^H) or N x m
+    const size_t gab = std::max(ozaki_gen_a_bytes(mc, op.N), ozaki_gen_a_bytes(op.N, mc));
+    if ((rc = ensure(ctx, ctx->ozGA, gab))) return rc;
+    if ((rc = ensure(ctx, ctx->ozGE, (size_t)(Np + 512) * sizeof(int)))) return rc;
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
     CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
@@ -315,28 +319,84 @@ int phase_filter(bsechase_ctx *ctx, const Hop &op, z_t *V, int64_t ldv, int m, c
 }
 
 // V -= L (L^H V)
+// The N x m products of QR and Rayleigh-Ritz: on the tensor cores with
+// FP64-level accuracy when the solve's products with H are (ctx->gen_tc),
+// else native FP64.  The operands here are orthonormal or unit-norm
+// columns, so the per-row/per-column scaling of the slices keeps the error
+// at FP64 rounding level.
+struct GenTcScope {
+    bsechase_ctx *c;
+    GenTcScope(bsechase_ctx *ctx, bool on) : c(ctx) { c->gen_tc = on; }
+    ~GenTcScope() { c->gen_tc = false; }
+};
+
+OzGemmWork gen_work(bsechase_ctx *ctx) {
+    OzGemmWork w;
+    w.A = ctx->ozGA.p;
+    w.a_bytes = ctx->ozGA.bytes;
+    w.E = (int *)ctx->ozGE.p;
+    w.e_len = (int64_t)(ctx->ozGE.bytes / sizeof(int));
+    w.B = ctx->ozB.p;
+    w.b_bytes = ctx->ozB.bytes;
+    w.F = (int *)ctx->ozF.p;
+    w.f_len = (int64_t)(ctx->ozF.bytes / sizeof(int));
+    w.P = (z_t *)ctx->ozP.p;
+    w.p_bytes = ctx->ozP.bytes;
+    return w;
+}
+
+// G (m1 x m2) = A^H B (+ shift on the diagonal, Hermitian part if hermitize)
+int gemm_cn(bsechase_ctx *ctx, int64_t m1, int64_t m2, int64_t K, const z_t *A, int64_t lda,
+            const z_t *B, int64_t ldb, z_t *G, int64_t ldg, double shift, int hermitize) {
+    if (ctx->gen_tc) {
+        const int mode = (m1 == m2 && (hermitize || shift != 0.0)) ? OZ_GRAM : OZ_PLAIN;
+        CK(ozaki_gemm(m1, (int)m2, K, A, lda, 1, B, ldb, mode, nullptr, 0, shift, hermitize, G, ldg,
+                      gen_work(ctx), ctx->sc, ctx->sms, ctx->st));
+    } else {
+        CK(launch_zgemm_cn(m1, m2, K, A, lda, B, ldb, G, ldg, shift, hermitize,
+                           (z_t *)ctx->part.p, kCnWork, ctx->st));
+    }
+    return BSE_OK;
+}
+
+// C (M x n) = A B, or D - A B with sub (D may alias C)
+int gemm_nn(bsechase_ctx *ctx, int64_t M, int64_t n, int64_t K, const z_t *A, int64_t lda,
+            const z_t *B, int64_t ldb, z_t *C, int64_t ldc, const z_t *D, int64_t ldd,
+            bool b_upper) {
+    if (ctx->gen_tc) {
+        CK(ozaki_gemm(M, (int)n, K, A, lda, 0, B, ldb, D ? OZ_SUB : OZ_PLAIN, D, ldd, 0.0, 0, C,
+                      ldc, gen_work(ctx), ctx->sc, ctx->sms, ctx->st));
+    } else {
+        GemmEpi ep{};
+        if (D) {
+            ep.mode = GEMM_SUB;
+            ep.D = D;
+            ep.ldd = ldd;
+        }
+        ep.b_upper = b_upper ? 1 : 0;
+        CK(launch_zgemm_nn(M, n, K, A, lda, B, ldb, C, ldc, ep, ctx->st));
+    }
+    return BSE_OK;
+}
+
 int project(bsechase_ctx *ctx, const z_t *L, int64_t ldl, int k, z_t *V, int64_t ldv, int64_t N,
             int m) {
     if (k <= 0) return BSE_OK;
     z_t *X = (z_t *)ctx->R.p;
-    CK(launch_zgemm_cn(k, m, N, L, ldl, V, ldv, X, k, 0.0, 0, (z_t *)ctx->part.p, kCnWork, ctx->st));
-    GemmEpi ep{};
-    ep.mode = GEMM_SUB;
-    ep.D = V;
-    ep.ldd = ldv;
-    CK(launch_zgemm_nn(N, m, k, L, ldl, X, k, V, ldv, ep, ctx->st));
-    return BSE_OK;
+    int rc;
+    if ((rc = gemm_cn(ctx, k, m, N, L, ldl, V, ldv, X, k, 0.0, 0))) return rc;
+    return gemm_nn(ctx, N, m, k, L, ldl, X, k, V, ldv, V, ldv, false);
 }
 
 // one Cholesky QR pass: G = V^H V + shift I = R^H R, V <- V R^{-1}
 int cholqr_pass(bsechase_ctx *ctx, z_t *V, int64_t ldv, int64_t N, int m, double shift) {
     z_t *G = (z_t *)ctx->G.p, *Ri = (z_t *)ctx->Ri.p, *B1 = (z_t *)ctx->B1.p;
-    CK(launch_zgemm_cn(m, m, N, V, ldv, V, ldv, G, m, shift, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    int rc;
+    if ((rc = gemm_cn(ctx, m, m, N, V, ldv, V, ldv, G, m, shift, 1))) return rc;
     CK(launch_cholesky(m, G, m, ctx->sc, ctx->st));
     CK(launch_trinv(m, G, m, Ri, m, ctx->st));
-    GemmEpi tri{};
-    tri.b_upper = 1;              // R^{-1} is upper triangular
-    CK(launch_zgemm_nn(N, m, m, V, ldv, Ri, m, B1, N, tri, ctx->st));
+    // R^{-1} is upper triangular
+    if ((rc = gemm_nn(ctx, N, m, m, V, ldv, Ri, m, B1, N, nullptr, 0, true))) return rc;
     CK(launch_copy_cols(N, m, B1, N, V, ldv, nullptr, ctx->st));
     return BSE_OK;
 }
@@ -367,11 +427,10 @@ int phase_rr(bsechase_ctx *ctx, const Hop &op, const z_t *Q, int64_t ldq, int m,
     GemmEpi plain{};
     int rc;
     if ((rc = hop_apply(ctx, op, m, Q, ldq, W, N, plain))) return rc;
-    CK(launch_zgemm_cn(m, m, N, Q, ldq, W, N, G, m, 0.0, 1, (z_t *)ctx->part.p, kCnWork, ctx->st));
+    if ((rc = gemm_cn(ctx, m, m, N, Q, ldq, W, N, G, m, 0.0, 1))) return rc;
     CK(launch_heev(m, G, m, theta, Yr, m, ctx->heev.p, ctx->sc, ctx->st));
-    CK(launch_zgemm_nn(N, m, m, Q, ldq, Yr, m, Vout, N, plain, ctx->st));
-    CK(launch_zgemm_nn(N, m, m, W, N, Yr, m, HVout, N, plain, ctx->st));
-    return BSE_OK;
+    if ((rc = gemm_nn(ctx, N, m, m, Q, ldq, Yr, m, Vout, N, nullptr, 0, false))) return rc;
+    return gemm_nn(ctx, N, m, m, W, N, Yr, m, HVout, N, nullptr, 0, false);
 }
 
 struct Timer {
@@ -438,6 +497,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     Hop op{H, N, ldh, precision_uses_tc(precision)};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
+    GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
     tm.mark(1);
     int64_t matvecs = (int64_t)std::min<int64_t>(o.lanczos_steps, N) * o.lanczos_vecs;
@@ -540,6 +600,14 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     }
     CK(cudaMemcpyAsync(s.order, order.data(), nev * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
     CK(launch_copy_cols(N, nev, V, N, d_evecs, ldz, s.order, ctx->st));
+    if (op.tc) {
+        // The Ritz vectors went through tensor-core products whose 48-bit
+        // slices leave an orthogonality error near 1e-12; one native FP64
+        // Cholesky QR pass of the nev output vectors (their Gram matrix is
+        // the identity to that level) restores FP64 orthonormality.
+        GenTcScope fp64(ctx, false);
+        if ((rc = cholqr_pass(ctx, (z_t *)d_evecs, ldz, N, nev, 0.0))) return rc;
+    }
     CK(launch_phase_normalize(N, nev, d_evecs, ldz, ctx->st));
     tm.mark(3);
     CK(cudaStreamSynchronize(ctx->st));
@@ -801,6 +869,7 @@ int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t l
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
            precision == CHASE_MIXED_FP32};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
+    GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_rr(ctx, op, (const z_t *)d_Q, ldq, m, s.theta, (z_t *)d_V, (z_t *)d_HV)))
         return rc;
     if (h_resid) {

@@ -27,6 +27,8 @@ struct bsechase_ctx {
     DevBuf V, B1, B2, B3, G, R, Ri, Yr, heev, small_d, ints, part, lz, tables, Hdev, Zdev;
     DevBuf ozA, ozE, ozB, ozF, ozP;  // tensor-core products: slices of H and of the operand,
                                      // split-K partials
+    DevBuf ozGA, ozGE;               // slices and exponents of op(A) for the general products
+    bool gen_tc = false;             // N x m products of QR and Rayleigh-Ritz on the tensor cores
     int sms = 0;                     // multiprocessors of the device
     OzakiH oh;
     int64_t wsN = 0;

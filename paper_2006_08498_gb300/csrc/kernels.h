@@ -53,6 +53,34 @@ size_t ozaki_a_bytes(int64_t N);
 size_t ozaki_b_bytes(int64_t N, int m);
 // workspace for split-K partial products of up to m columns
 size_t ozaki_partial_bytes(int64_t N, int m);
+
+// General FP64-accurate products on the tensor cores (same kernel and
+// slicing as the product with H): C (M x n) = out(op(A) B), op(A) = A
+// (M x K) or A^H (ah = 1: A is K x M); B is K x n.  out: OZ_PLAIN C = op(A)B,
+// OZ_SUB C = D - op(A)B (D may alias C), OZ_GRAM (M = n) C = op(A)B, its
+// Hermitian part if hermitize, plus shift on the diagonal.  Workspace:
+// slices of op(A) (ozaki_gen_a_bytes) with M-long exponents E, slices of B
+// (ozaki_gen_b_bytes) with n-long exponents F, FP64 partials of n M
+// complex values per split.
+enum { OZ_PLAIN = 0, OZ_SUB = 1, OZ_GRAM = 2 };
+struct OzGemmWork {
+    void *A = nullptr;
+    size_t a_bytes = 0;
+    int *E = nullptr;
+    int64_t e_len = 0;
+    void *B = nullptr;
+    size_t b_bytes = 0;
+    int *F = nullptr;
+    int64_t f_len = 0;
+    z_t *P = nullptr;
+    size_t p_bytes = 0;
+};
+size_t ozaki_gen_a_bytes(int64_t M, int64_t K);
+size_t ozaki_gen_b_bytes(int64_t K, int n);
+cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, int ah,
+                       const z_t *B, int64_t ldb, int mode, const z_t *D, int64_t ldd,
+                       double shift, int hermitize, z_t *C, int64_t ldc, const OzGemmWork &w,
+                       ChaseScalars *sc, int sms, cudaStream_t st);
 // Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
 cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
                             cudaStream_t st);

@@ -111,12 +111,12 @@ __device__ __forceinline__ float slice_value(int t, int p) {
 // exponent of |re| and |im|; INT_MIN for an all-zero line.
 // Non-finite entries cannot be sliced; they are reported through the
 // error word (fmax alone would skip NaN).
-__global__ void k_row_exponent(int64_t N, const z_t *__restrict__ H, int64_t ldh, int *E,
-                               int cols_per_block, ChaseScalars *sc) {
+__global__ void k_row_exponent(int64_t M, int64_t K, const z_t *__restrict__ H, int64_t ldh,
+                               int *E, int cols_per_block, ChaseScalars *sc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= M) return;
     const int64_t k0 = (int64_t)blockIdx.y * cols_per_block;
-    const int64_t k1 = (k0 + cols_per_block < N) ? k0 + cols_per_block : N;
+    const int64_t k1 = (k0 + cols_per_block < K) ? k0 + cols_per_block : K;
     double mx = 0.0;
     bool finite = true;
     for (int64_t k = k0; k < k1; k++) {
@@ -169,31 +169,57 @@ __host__ __device__ __forceinline__ int64_t tiled_index(int part, int64_t k, int
     return (((int64_t)part * nch + k / 64) * rows + row) * 64 + (k % 64);
 }
 
-// A slices of H: slice p of re/im H_ik at tiled_index(p*2 + ri, k, i).  32 x 32 tiles through shared memory; padded rows and columns
-// (>= N) are written as zeros.
-__global__ void k_slice_h(int64_t N, int64_t Np, const z_t *__restrict__ H, int64_t ldh,
-                          const int *__restrict__ E, uint16_t *A) {
+// A slices of an M x K matrix H (rows padded to Mp, K to Kp): slice p of
+// re/im H_ik at tiled_index(p*2 + ri, k, i, Kp, Mp).  32 x 32 tiles through
+// shared memory; padded rows and columns are written as zeros.
+__global__ void k_slice_h(int64_t M, int64_t Mp, int64_t K, int64_t Kp,
+                          const z_t *__restrict__ H, int64_t ldh, const int *__restrict__ E,
+                          uint16_t *A) {
     __shared__ z_t tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
     for (int r = ty; r < 32; r += 8) {
         const int64_t i = i0 + tx, k = k0 + r;       // column k, rows i: coalesced
-        tile[r][tx] = (i < N && k < N) ? H[i + k * ldh] : zmk(0.0, 0.0);
+        tile[r][tx] = (i < M && k < K) ? H[i + k * ldh] : zmk(0.0, 0.0);
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int64_t i = i0 + r, k = k0 + tx;       // row i, consecutive k
         const z_t h = tile[tx][r];
-        int e = (i < N) ? E[i] : INT_MIN;
+        int e = (i < M) ? E[i] : INT_MIN;
         if (e == INT_MIN) e = 0;
         int tr[kS], ti[kS];
         split_digits(h.x, e, tr);
         split_digits(h.y, e, ti);
 #pragma unroll
         for (int p = 0; p < kS; p++) {
-            A[tiled_index(p * 2 + 0, k, i, Np, Np)] = bf16_exact(slice_value(tr[p], p));
-            A[tiled_index(p * 2 + 1, k, i, Np, Np)] = bf16_exact(slice_value(ti[p], p));
+            A[tiled_index(p * 2 + 0, k, i, Kp, Mp)] = bf16_exact(slice_value(tr[p], p));
+            A[tiled_index(p * 2 + 1, k, i, Kp, Mp)] = bf16_exact(slice_value(ti[p], p));
         }
+    }
+}
+
+// A slices of op(A) = A^H for a K x M matrix A: op(A)_ik = conj(A_ki), read
+// down column i of A (coalesced in k); exponents E[i] are those of column i.
+__global__ void k_slice_ah(int64_t M, int64_t Mp, int64_t K, int64_t Kp,
+                           const z_t *__restrict__ A, int64_t lda, const int *__restrict__ E,
+                           uint16_t *S) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = blockIdx.y;
+    if (k >= Kp || i >= Mp) return;
+    z_t a = zmk(0.0, 0.0);
+    int e = 0;
+    if (i < M && k < K) {
+        a = A[k + i * lda];
+        e = E[i] == INT_MIN ? 0 : E[i];
+    }
+    int tr[kS], ti[kS];
+    split_digits(a.x, e, tr);
+    split_digits(-a.y, e, ti);
+#pragma unroll
+    for (int p = 0; p < kS; p++) {
+        S[tiled_index(p * 2 + 0, k, i, Kp, Mp)] = bf16_exact(slice_value(tr[p], p));
+        S[tiled_index(p * 2 + 1, k, i, Kp, Mp)] = bf16_exact(slice_value(ti[p], p));
     }
 }
 
@@ -573,6 +599,31 @@ __global__ void k_split_reduce(int64_t M, int n, int nsplit, const z_t *__restri
     C[i + j * ldc] = v;
 }
 
+// General products: C = out(sum over splits z of P[z]) in increasing z.
+// OZ_PLAIN: C = S; OZ_SUB: C = D - S (D may alias C); OZ_GRAM (square):
+// C = S, or its Hermitian part (S + S^H)/2, plus shift on the diagonal.
+__global__ void k_gen_reduce(int64_t M, int n, int nsplit, const z_t *__restrict__ P, int mode,
+                             const z_t *D, int64_t ldd, double shift, int hermitize, z_t *C,
+                             int64_t ldc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= M) return;
+    z_t v = zmk(0.0, 0.0);
+    for (int z = 0; z < nsplit; z++) v = zadd(v, P[((int64_t)z * n + j) * M + i]);
+    if (mode == OZ_SUB) {
+        v = zsub(D[i + j * ldd], v);
+    } else if (mode == OZ_GRAM) {
+        if (hermitize) {
+            z_t t = zmk(0.0, 0.0);
+            for (int z = 0; z < nsplit; z++) t = zadd(t, P[((int64_t)z * n + i) * M + j]);
+            v = zmk(0.5 * (v.x + t.x), 0.5 * (v.y - t.y));
+            if (i == j) v.y = 0.0;
+        }
+        if (i == j) v.x += shift;
+    }
+    C[i + j * ldc] = v;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -605,6 +656,30 @@ bool make_map(CUtensorMap *m, void *base, uint64_t rows, uint64_t tiles, uint32_
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Split K into `sp` ranges so that the units (tiles x splits) spread
+// evenly over one persistent CTA per SM.  Cost in K-chunk units: the
+// busiest CTA's units, each with half a chunk of pipeline fill and drain,
+// plus the FP64 partials written and summed by the reduction (32 bytes per
+// complex output and split, at about one chunk per 6 us and 6 TB/s).  At
+// least 16 K chunks per split, partials within the workspace; 0 if even one
+// split does not fit.
+int choose_splits(int tiles, int nchunks, int n, int64_t M, size_t partial_bytes, int sms) {
+    if ((int64_t)n * M * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) return 0;
+    int best = 1;
+    double best_t = 1e30;
+    for (int sp = 1; sp <= 32; sp++) {
+        if ((int64_t)sp * 16 > nchunks && sp > 1) break;
+        if ((int64_t)sp * n * M * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) break;
+        const int64_t u = (int64_t)tiles * sp;
+        const int64_t per = (u + sms - 1) / sms;
+        const double chunks = (double)((nchunks + sp - 1) / sp);
+        const double part = (double)sp * n * M * 32.0 / (6.0e12 * 6.0e-6);
+        const double t = (double)per * (chunks + 0.5) + part;
+        if (t < best_t - 1e-9) { best_t = t; best = sp; }
+    }
+    return best;
+}
+
 }  // namespace
 
 int64_t ozaki_padded(int64_t N) { return (N + 127) / 128 * 128; }
@@ -634,10 +709,10 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     bse_count_launches(1);
     const int cpb = 256;
     dim3 g1((unsigned)((N + 255) / 256), (unsigned)((N + cpb - 1) / cpb));
-    k_row_exponent<<<g1, 256, 0, st>>>(N, H, ldh, oh->E, cpb, sc);
+    k_row_exponent<<<g1, 256, 0, st>>>(N, N, H, ldh, oh->E, cpb, sc);
     bse_count_launches(1);
     dim3 g2((unsigned)(Np / 32), (unsigned)(Np / 32));
-    k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
+    k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
     bse_count_launches(1);
     if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * (Np / kKC)),
                   kBM))
@@ -686,35 +761,16 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.E = oh.E;
     a.F = F;
     a.sc = sc;
-    // Split K into `sp` ranges so that the units (tiles x splits) spread
-    // evenly over one persistent CTA per SM.  Cost in K-chunk units: the
-    // busiest CTA's units, each with half a chunk of pipeline fill and
-    // drain, plus the FP64 partials written and summed by k_split_reduce
-    // (32 bytes per complex output and split, at about one chunk per 6 us
-    // and 6 TB/s).
-    // At least 16 K chunks per split, partials within the workspace.
     const int tx = mp / kW, ty = (int)(Np / kBM);
-    const int tiles = tx * ty;
-    int best = 1;
-    double best_t = 1e30;
-    if ((int64_t)n * N * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) return cudaErrorInvalidValue;
-    for (int sp = 1; sp <= 32; sp++) {
-        if ((int64_t)sp * 16 > a.nchunks && sp > 1) break;
-        if ((int64_t)sp * n * N * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) break;
-        const int64_t u = (int64_t)tiles * sp;
-        const int64_t per = (u + sms - 1) / sms;
-        const double chunks = (double)((a.nchunks + sp - 1) / sp);
-        const double part = (double)sp * n * N * 32.0 / (6.0e12 * 6.0e-6);
-        const double t = (double)per * (chunks + 0.5) + part;
-        if (t < best_t - 1e-9) { best_t = t; best = sp; }
-    }
+    const int best = choose_splits(tx * ty, a.nchunks, n, N, partial_bytes, sms);
+    if (best < 1) return cudaErrorInvalidValue;
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
     a.P = partials;
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
-    const int64_t units = (int64_t)tiles * nsplit;
+    const int64_t units = (int64_t)tx * ty * nsplit;
     dim3 grid((unsigned)std::min<int64_t>(units, sms));
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
     if (ev0) cudaEventRecord(ev0, st);
@@ -724,6 +780,79 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
     k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, partials, ep, Y, ldy, C, ldc);
+    bse_count_launches(1);
+    return cudaGetLastError();
+}
+
+size_t ozaki_gen_a_bytes(int64_t M, int64_t K) {
+    const int64_t Mp = (M + kBM - 1) / kBM * kBM, Kp = (K + kKC - 1) / kKC * kKC;
+    return (size_t)kS * 2 * Mp * Kp * 2;
+}
+
+size_t ozaki_gen_b_bytes(int64_t K, int n) {
+    const int64_t Kp = (K + kKC - 1) / kKC * kKC;
+    const int64_t mp = (n + kW - 1) / kW * kW;
+    return (size_t)kS * 3 * mp * Kp * 2;
+}
+
+cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, int ah,
+                       const z_t *B, int64_t ldb, int mode, const z_t *D, int64_t ldd,
+                       double shift, int hermitize, z_t *C, int64_t ldc, const OzGemmWork &w,
+                       ChaseScalars *sc, int sms, cudaStream_t st) {
+    if (M <= 0 || n <= 0) return cudaSuccess;
+    if (K <= 0 || (mode == OZ_GRAM && M != n)) return cudaErrorInvalidValue;
+    const int64_t Mp = (M + kBM - 1) / kBM * kBM, Kp = (K + kKC - 1) / kKC * kKC;
+    const int mp = (n + kW - 1) / kW * kW;
+    if (ozaki_gen_a_bytes(M, K) > w.a_bytes || Mp > w.e_len || ozaki_gen_b_bytes(K, n) > w.b_bytes ||
+        mp > w.f_len)
+        return cudaErrorInvalidValue;
+    // exponents and slices of op(A): rows of A, or columns of A for A^H
+    k_fill_int<<<(unsigned)((Mp + 255) / 256), 256, 0, st>>>(w.E, (int)Mp, INT_MIN);
+    if (ah) {
+        dim3 ge((unsigned)std::min<int64_t>((K + 255) / 256, 16), (unsigned)M);
+        k_col_exponent<<<ge, 256, 0, st>>>(K, (int)M, A, lda, w.E, sc);
+        dim3 gs((unsigned)((Kp + 255) / 256), (unsigned)Mp);
+        k_slice_ah<<<gs, 256, 0, st>>>(M, Mp, K, Kp, A, lda, w.E, (uint16_t *)w.A);
+    } else {
+        const int cpb = 256;
+        dim3 g1((unsigned)((M + 255) / 256), (unsigned)((K + cpb - 1) / cpb));
+        k_row_exponent<<<g1, 256, 0, st>>>(M, K, A, lda, w.E, cpb, sc);
+        dim3 g2((unsigned)(Kp / 32), (unsigned)(Mp / 32));
+        k_slice_h<<<g2, dim3(32, 8), 0, st>>>(M, Mp, K, Kp, A, lda, w.E, (uint16_t *)w.A);
+    }
+    // exponents and slices of B (K x n)
+    k_fill_int<<<(mp + 255) / 256, 256, 0, st>>>(w.F, mp, INT_MIN);
+    dim3 ge((unsigned)std::min<int64_t>((K + 255) / 256, 16), (unsigned)n);
+    k_col_exponent<<<ge, 256, 0, st>>>(K, n, B, ldb, w.F, sc);
+    dim3 gs((unsigned)((Kp + 255) / 256), (unsigned)mp);
+    k_slice_y<<<gs, 256, 0, st>>>(K, Kp, n, mp, B, ldb, w.F, (uint16_t *)w.B);
+    bse_count_launches(6);
+    CUtensorMap tmA, tmB;
+    if (!make_map(&tmA, w.A, (uint64_t)Mp, (uint64_t)(kS * 2 * (Kp / kKC)), kBM) ||
+        !make_map(&tmB, w.B, (uint64_t)mp, (uint64_t)(kS * 3 * (Kp / kKC)), kW))
+        return cudaErrorInvalidValue;
+    OzArgs a;
+    a.M = M;
+    a.n = n;
+    a.mp = mp;
+    a.nchunks = (int)(Kp / kKC);
+    a.E = w.E;
+    a.F = w.F;
+    a.sc = sc;
+    const int tx = mp / kW, ty = (int)(Mp / kBM);
+    const int best = choose_splits(tx * ty, a.nchunks, n, M, w.p_bytes, sms);
+    if (best < 1) return cudaErrorInvalidValue;
+    a.csplit = (a.nchunks + best - 1) / best;
+    const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
+    a.P = w.P;
+    a.tx = tx;
+    a.ty = ty;
+    a.tz = nsplit;
+    dim3 grid((unsigned)std::min<int64_t>((int64_t)tx * ty * nsplit, sms));
+    cudaError_t e = launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
+    if (e != cudaSuccess) return e;
+    dim3 gr((unsigned)((M + 255) / 256), (unsigned)n);
+    k_gen_reduce<<<gr, 256, 0, st>>>(M, n, nsplit, w.P, mode, D, ldd, shift, hermitize, C, ldc);
     bse_count_launches(1);
     return cudaGetLastError();
 }

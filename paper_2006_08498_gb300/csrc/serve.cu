@@ -86,6 +86,8 @@ size_t estimate_run_bytes(int64_t N, int m, int nev, int precision) {
         b += 24 * Np * Np;                                  // slices of H
         b += 36 * mp * Np;                                  // slices of the operand
         b += ozaki_partial_bytes(N, std::max(m, 32));       // split-K partials
+        b += std::max(ozaki_gen_a_bytes(std::max(m, 32), N),  // slices of op(A) in the
+                      ozaki_gen_a_bytes(N, std::max(m, 32))); // QR / Rayleigh-Ritz products
     }
     return b;
 }

@@ -338,7 +338,10 @@ def test_solve_mixed_precision(ctx, c1):
     _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
     assert np.max(resid) <= 1e-10
     assert 0 < st["filter_matvecs_low"] < st["filter_matvecs"]
-    assert np.max(np.abs(evals - e64) / np.abs(e64)) <= 1e-12
+    # both solves take their Ritz values from tensor-core products with
+    # 48-bit slices (relative to row / column maxima, |H| ~ 14 here), so they
+    # agree to a few 1e-12; both are within 1e-10 of the exact eigenvalues
+    assert np.max(np.abs(evals - e64) / np.abs(e64)) <= 5e-12
 
 
 def test_solve_is_deterministic(ctx):
