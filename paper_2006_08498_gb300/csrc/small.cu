@@ -75,32 +75,90 @@ __global__ void __launch_bounds__(kST) k_cholesky(int n, z_t *G, int64_t ld, Cha
     }
 }
 
-// ------------------------------------------------- triangular inverse
-// Column j of X = R^{-1} by column-oriented back substitution of R x = e_j.
+
+// Cholesky with the upper triangle in shared memory (n <= kCholSmemN):
+// packed column-major, element (i, j), i <= j, at j (j + 1) / 2 + i.  The
+// same left-looking order as k_cholesky; every dot product now reads shared
+// memory instead of L2, which was what bounded the global version.
+constexpr int kCholSmemN = 160;
+
+__device__ __forceinline__ int upk(int i, int j) { return j * (j + 1) / 2 + i; }
+
 __global__ void __launch_bounds__(kST)
-k_trinv(int n, const z_t *__restrict__ R, int64_t ldr, z_t *X, int64_t ldx) {
+k_cholesky_smem(int n, z_t *G, int64_t ld, ChaseScalars *sc) {
+    extern __shared__ z_t U[];
+    __shared__ int failed;
+    __shared__ double rjj_s;
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    for (int j = warp; j < n; j += kSW) {
-        z_t *x = X + (int64_t)j * ldx;
-        for (int r = lane; r < n; r += 32) x[r] = zmk(r == j ? 1.0 : 0.0, 0.0);
-        __syncwarp();
-        for (int k = j; k >= 0; k--) {
-            z_t xk;
-            if (lane == 0) {
-                const z_t rkk = R[k + (int64_t)k * ldr];
-                const double inv = 1.0 / rkk.x;   // real positive diagonal
-                xk = zscale(x[k], inv);
-                x[k] = xk;
-            }
-            __syncwarp();
-            xk = x[k];
-            for (int r = lane; r < k; r += 32) {
-                const z_t rk = R[r + (int64_t)k * ldr];
-                x[r] = zsub(x[r], zmul(rk, xk));
-            }
-            __syncwarp();
-        }
+    if (threadIdx.x == 0) failed = 0;
+    for (int e = threadIdx.x; e < n * n; e += kST) {
+        const int i = e % n, j = e / n;
+        if (i <= j) U[upk(i, j)] = G[i + (int64_t)j * ld];
     }
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const z_t *cj = U + upk(0, j);
+        if (warp == 0) {
+            double s = 0.0;
+            for (int k = lane; k < j; k += 32) s += zabs2(cj[k]);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double d = cj[j].x - s;
+                if (!(d > 0.0)) {
+                    failed = 1;
+                    set_error(sc, DEV_CHOL_FAIL, j);
+                } else {
+                    rjj_s = sqrt(d);
+                    U[upk(j, j)] = zmk(rjj_s, 0.0);
+                }
+            }
+        }
+        __syncthreads();
+        if (failed) return;
+        const double inv = 1.0 / rjj_s;
+        for (int i = j + 1 + warp; i < n; i += kSW) {
+            const z_t *ci = U + upk(0, i);
+            z_t s = zmk(0.0, 0.0);
+            for (int k = lane; k < j; k += 32) zcfma(s, cj[k], ci[k]);
+            s.x = warp_sum(s.x);
+            s.y = warp_sum(s.y);
+            if (lane == 0) U[upk(j, i)] = zscale(zsub(U[upk(j, i)], s), inv);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += kST) {
+        const int i = e % n, j = e / n;
+        G[i + (int64_t)j * ld] = (i <= j) ? U[upk(i, j)] : zmk(0.0, 0.0);
+    }
+}
+
+// X = R^{-1} for upper triangular R with a real positive diagonal: one warp
+// per column j (8 per CTA, as many CTAs as needed), column-oriented back
+// substitution of R x = e_j with x in shared memory and the reciprocals of
+// the diagonal computed once per CTA.
+__global__ void __launch_bounds__(256)
+k_trinv_cols(int n, const z_t *__restrict__ R, int64_t ldr, z_t *X, int64_t ldx) {
+    extern __shared__ double smt[];
+    double *rinv = smt;                                   // n
+    z_t *xs = (z_t *)(smt + ((n + 1) & ~1));              // 8 x n
+    const int lane = threadIdx.x % 32, wl = threadIdx.x / 32;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) rinv[k] = 1.0 / R[k + (int64_t)k * ldr].x;
+    __syncthreads();
+    const int j = blockIdx.x * 8 + wl;
+    if (j >= n) return;
+    z_t *x = xs + (int64_t)wl * n;
+    for (int r = lane; r < n; r += 32) x[r] = zmk(r == j ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    for (int k = j; k >= 0; k--) {
+        const z_t xk = zscale(x[k], rinv[k]);
+        __syncwarp();
+        if (lane == 0) x[k] = xk;
+        const z_t *rk = R + (int64_t)k * ldr;
+        for (int r = lane; r < k; r += 32) x[r] = zsub(x[r], zmul(rk[r], xk));
+        __syncwarp();
+    }
+    z_t *xo = X + (int64_t)j * ldx;
+    for (int r = lane; r < n; r += 32) xo[r] = x[r];
 }
 
 // ------------------------------------------------- Hermitian eigensolver
@@ -762,14 +820,35 @@ __global__ void k_chase_update(int m_act, int nev, double tol, int deg_max,
 
 cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_cholesky<<<1, kST, 0, st>>>(n, G, ld, sc);
+    if (n <= kCholSmemN) {
+        const int bytes = (kCholSmemN * (kCholSmemN + 1) / 2) * (int)sizeof(z_t);
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_cholesky_smem<<<1, kST, (size_t)(n * (n + 1) / 2) * sizeof(z_t), st>>>(n, G, ld, sc);
+    } else {
+        k_cholesky<<<1, kST, 0, st>>>(n, G, ld, sc);
+    }
     bse_count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_trinv<<<1, kST, 0, st>>>(n, R, ldr, X, ldx);
+    const size_t bytes = (size_t)((n + 1) & ~1) * sizeof(double) + (size_t)8 * n * sizeof(z_t);
+    static bool attr = false;
+    if (!attr) {
+        const int maxb = (int)(((kMaxN + 1) & ~1) * sizeof(double) + 8 * kMaxN * sizeof(z_t));
+        cudaError_t e = cudaFuncSetAttribute(k_trinv_cols,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_trinv_cols<<<(n + 7) / 8, 256, bytes, st>>>(n, R, ldr, X, ldx);
     bse_count_launches(1);
     return cudaGetLastError();
 }
