@@ -439,6 +439,37 @@ def test_solve_full_size_certified(ctx):
     assert 2 <= st["iters"] <= 20
 
 
+def test_solve_c3_certified(ctx):
+    """N = 50000 (Nk = 3125), nev = 200, nex = 80, tol 1e-10, degree groups of
+    48 (the large configuration).  No dense oracle is feasible here; the
+    result is certified by properties that hold at any size: residuals of
+    sampled pairs recomputed with the native FP64 product (Weyl: each
+    eigenvalue is then within its residual of the spectrum), orthonormality,
+    and a second solve from other start vectors in the mixed precision mode
+    reaching the same eigenvalues."""
+    Nk, nev, nex = 3125, 200, 80
+    Hd = ctx.build_hamiltonian(0, Nk, 4, 4)
+    evals, Vd, resid, st = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36, degree_group=48)
+    assert np.all(np.diff(evals) >= 0) and np.max(resid) <= 1e-10
+    normH = st["norm_est"]
+    cols = [0, 1, 57, 99, 100, 150, 198, 199]
+    Vs = pkg.colmajor_empty(Vd.shape[0], len(cols), device=Vd.device)
+    Vs.copy_(Vd[:, cols])
+    HV = ctx.hemm(Hd, Vs, precision=pkg.CHASE_FP64_DFMA)
+    lam = torch.tensor(evals[cols], dtype=torch.complex128, device=Vs.device)
+    rn = torch.linalg.norm(HV - Vs * lam, dim=0).cpu().numpy()
+    assert np.max(rn) / normH <= 1e-9
+    G = ctx.gram(Vd, Vd)
+    eye = torch.eye(nev, dtype=torch.complex128, device=G.device)
+    assert torch.linalg.norm(G - eye).item() <= 1e-11
+    e2, V2, r2, st2 = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36, seed=1,
+                                precision=pkg.CHASE_MIXED_FP32, degree_group=48)
+    assert np.max(r2) <= 1e-10
+    assert np.max(np.abs(e2 - evals) / np.abs(evals)) <= 1e-10
+    del Hd, Vd, V2
+    torch.cuda.empty_cache()
+
+
 def test_solve_grouped_degrees_matches_oracle(ctx, c1):
     """degree_group = 48: the same eigenpairs as the oracle's ChASE with the
     same grouping (and as the dense oracle), iterations within one."""
