@@ -120,6 +120,26 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def replica_seed(base_seed, rank):
+    """Seed of rank `rank`'s replica: every rank solves its own Hamiltonian."""
+    return base_seed + rank
+
+
+def slowest(value, dist=None, device="cpu"):
+    """The largest `value` over the ranks (the bench reports the slowest)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, ms_max):
+    """Solves per second of the whole job: every rank finished `steps`
+    replicas within the slowest rank's time."""
+    return world * steps / (ms_max / 1e3)
+
+
 def workload(args):
     """The benchmark workload, with optional overrides for profiling runs."""
     W = dict(WORKLOAD)
@@ -248,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
     prec = PRECISIONS[args.precision]
 
     def step():
-        ctx.build_hamiltonian(W["seed"] + rank, W["Nk"], W["Nv"], W["Nc"], out=H)
+        ctx.build_hamiltonian(replica_seed(W["seed"], rank), W["Nk"], W["Nv"], W["Nc"], out=H)
         return ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs,
                          precision=prec, degree_group=args.degree_group)
 
@@ -271,10 +291,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     ck = clocks.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = slowest(ms, dist, device="cuda")
 
     # end to end through the host-buffer entry point: pinned H in, eigenvectors
     # and eigenvalues out, one call per step (the device path is already warm)
@@ -289,11 +306,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(e2e_steps):
             ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh,
                            precision=prec, degree_group=args.degree_group)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_s = float(te.item())
+        e2e_s = slowest((time.perf_counter() - t0) / e2e_steps, dist, device="cuda")
 
     if rank == 0:
         st = stats[-1]
@@ -306,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": dict(W, precision=args.precision, degree_group=args.degree_group,
                            parallelism="replicas" if world > 1 else "single"),
-            "throughput_solves_per_s": world * args.steps / (ms_max / 1e3),
+            "throughput_solves_per_s": replica_throughput(world, args.steps, ms_max),
             "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs",
                                          "filter_matvecs_low", "filter_launches", "ms_lanczos",
                                          "ms_filter", "ms_qr", "ms_rr", "ms_resid",
