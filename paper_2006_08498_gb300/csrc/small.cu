@@ -13,6 +13,8 @@
 //     per-vector degrees of Eq. (S1) and their sort.
 // They run on one SM and read/write global memory (L2 resident at these
 // sizes).  Failures set an error word instead of trapping.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -21,6 +23,7 @@ namespace {
 constexpr int kST = 1024;                 // threads of the small kernels
 constexpr int kSW = kST / 32;             // warps
 constexpr int kMaxN = 512;                // largest reduced problem
+static_assert(kSW == 32, "block_sum sums one partial per lane");
 
 __device__ double block_sum(double v, double *red) {
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
@@ -28,9 +31,12 @@ __device__ double block_sum(double v, double *red) {
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < kSW; w++) s += red[w];  // same order in every thread
-    return s;
+    if (warp == 0) {            // one warp sums the partials; FP64 issue is scarce
+        const double s = warp_sum(red[lane]);
+        if (lane == 0) red[kSW] = s;
+    }
+    __syncthreads();
+    return red[kSW];
 }
 
 // ------------------------------------------------------------ Cholesky
@@ -244,7 +250,7 @@ __host__ __device__ inline size_t heev_bytes(int n) {
 
 __global__ void __launch_bounds__(kST)
 k_heev_reduce(int n, z_t *A, int64_t lda, HeevWork w) {
-    __shared__ double red[kSW];
+    __shared__ double red[kSW + 1];
     __shared__ double s_tau, s_K;
     __shared__ z_t s_beta;
     const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
@@ -326,6 +332,233 @@ k_heev_reduce(int n, z_t *A, int64_t lda, HeevWork w) {
             w.delta[k + 1] = (ae > 0.0) ? zmul(w.delta[k], zscale(w.esub[k], 1.0 / ae)) : w.delta[k];
         }
     }
+}
+
+// The same reduction spread over a thread-block cluster of C CTAs (one per
+// SM).  FP64 issue on one SM bounds the single-CTA version, so the trailing
+// block is distributed: global column j lives in the shared memory of CTA
+// j mod C, packed (rows j..n-1).  Step k of Sec. "RR" reduction:
+//   the owner of column k forms v_k and tau_k and publishes them in its
+//   shared memory; cluster barrier;
+//   every CTA reads v_k, forms its partial of B v over the columns it
+//   holds (a column axpy for rows >= j and a dot for the mirrored upper part);
+//   cluster barrier;
+//   every CTA sums the C partials in rank order (the same p everywhere), forms
+//   q = p - (tau/2)(v^H p) v and updates its own columns; the owner of column
+//   k + 1 then forms v_{k+1}.
+// Control flow is uniform across the cluster (tau is read from the owner by
+// every CTA), so every thread reaches every cluster barrier.
+constexpr int kHhT = 256;                 // threads per CTA
+constexpr int kHhW = kHhT / 32;
+constexpr int kHhMaxCols = 64;            // own columns of one CTA (n <= 512, C >= 8)
+
+__device__ double hh_block_sum(double v, double *red) {
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double s = (lane < kHhW) ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) red[kHhW] = s;
+    }
+    __syncthreads();
+    return red[kHhW];
+}
+
+template <int C>
+__host__ __device__ constexpr int hh_cols(int n, int c) { return (c < n) ? (n - c + C - 1) / C : 0; }
+// start of local column l of rank c in the packed store
+template <int C>
+__host__ __device__ constexpr int hh_base(int n, int c, int l) { return l * n - C * l * (l - 1) / 2 - c * l; }
+
+template <int C>
+__global__ void __launch_bounds__(kHhT)
+k_heev_reduce_cl(int n, const z_t *A, int64_t lda, HeevWork w) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ z_t Bl[];                 // own columns, packed
+    __shared__ z_t s_vo[2][kMaxN];              // v published by the column owner
+    __shared__ z_t s_pp[kMaxN];                 // this CTA's partial of B v
+    __shared__ z_t s_v[kMaxN], s_q[kMaxN];
+    __shared__ z_t s_t[kHhMaxCols];
+    __shared__ double s_tau[2];
+    __shared__ double red[kHhW + 1];
+    __shared__ z_t s_beta;
+    const int c = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    const int ncol = hh_cols<C>(n, c);
+
+    for (int l = 0; l < ncol; l++) {
+        const int j = l * C + c;
+        z_t *col = Bl + hh_base<C>(n, c, l);
+        for (int r = j + tid; r < n; r += kHhT) col[r - j] = A[r + (int64_t)j * lda];
+    }
+    __syncthreads();
+
+    // Householder vector of column k (called by every thread of its owner)
+    auto house = [&](int k) {
+        const int L = n - k - 1;
+        const z_t *x = Bl + hh_base<C>(n, c, k / C) + 1;   // rows k+1 .. n-1
+        double part = 0.0;
+        for (int i = tid; i < L; i += kHhT) part += zabs2(x[i]);
+        const double alpha = sqrt(hh_block_sum(part, red));
+        if (tid == 0) {
+            const z_t x0 = x[0];
+            double tau = 0.0;
+            z_t beta = x0;
+            if (L > 1 && alpha != 0.0) {
+                const double ax0 = sqrt(zabs2(x0));
+                const z_t ph = (ax0 > 0.0) ? zscale(x0, 1.0 / ax0) : zmk(1.0, 0.0);
+                beta = zscale(ph, -alpha);
+                tau = 1.0 / (alpha * (alpha + ax0));   // 2 / (v^H v)
+            }
+            w.esub[k] = beta;
+            w.tau[k] = tau;
+            s_beta = beta;
+            s_tau[k & 1] = tau;
+        }
+        __syncthreads();
+        if (s_tau[k & 1] != 0.0) {
+            z_t *vg = w.V + (k + 1) + (int64_t)k * n;
+            for (int i = tid; i < L; i += kHhT) {
+                const z_t vi = (i == 0) ? zsub(x[0], s_beta) : x[i];
+                s_vo[k & 1][i] = vi;
+                vg[i] = vi;
+            }
+        }
+    };
+
+    if (c == 0 && n >= 2) house(0);
+    for (int k = 0; k + 1 < n; k++) {
+        const int L = n - k - 1, b0 = k + 1, o = k % C;
+        cl.sync();                                            // v_k published
+        const double tau = *cl.map_shared_rank(&s_tau[k & 1], o);
+        const int l0 = (b0 > c) ? (b0 - c + C - 1) / C : 0;  // first own column >= b0
+        if (tau != 0.0) {
+            const z_t *vo = cl.map_shared_rank(&s_vo[k & 1][0], o);
+            for (int i = tid; i < L; i += kHhT) s_v[i] = vo[i];
+            __syncthreads();
+            // mirrored part: t_j = sum_{r > j} conj(B_rj) v_r for own columns j
+            for (int l = l0 + warp; l < ncol; l += kHhW) {
+                const int j = l * C + c;
+                const z_t *col = Bl + hh_base<C>(n, c, l);
+                z_t s = zmk(0.0, 0.0);
+                for (int r = j + 1 + lane; r < n; r += 32) zcfma(s, col[r - j], s_v[r - b0]);
+                s.x = warp_sum(s.x);
+                s.y = warp_sum(s.y);
+                if (lane == 0) s_t[l] = s;
+            }
+            // lower part: s_r = sum_{own j <= r} B_rj v_j
+            for (int i = tid; i < L; i += kHhT) {
+                const int r = b0 + i;
+                z_t s = zmk(0.0, 0.0);
+                for (int l = l0; l < ncol; l++) {
+                    const int j = l * C + c;
+                    if (j > r) break;
+                    zfma(s, Bl[hh_base<C>(n, c, l) + (r - j)], s_v[j - b0]);
+                }
+                s_pp[i] = s;
+            }
+            __syncthreads();
+            for (int i = tid; i < L; i += kHhT) {
+                const int r = b0 + i;
+                if (r % C == c) s_pp[i] = zadd(s_pp[i], s_t[r / C]);
+            }
+        }
+        cl.sync();                                            // partials published
+        if (tau != 0.0) {
+            for (int i = tid; i < L; i += kHhT) {
+                z_t s = zmk(0.0, 0.0);
+                for (int cc = 0; cc < C; cc++) s = zadd(s, cl.map_shared_rank(s_pp, cc)[i]);
+                s_q[i] = zscale(s, tau);                      // p = tau B v
+            }
+            double vp = 0.0;   // Re(v^H p)
+            for (int i = tid; i < L; i += kHhT) vp += s_v[i].x * s_q[i].x + s_v[i].y * s_q[i].y;
+            const double K = 0.5 * tau * hh_block_sum(vp, red);
+            for (int i = tid; i < L; i += kHhT) s_q[i] = zsub(s_q[i], zscale(s_v[i], K));
+            __syncthreads();
+            // B -= v q^H + q v^H on the own columns (rows >= j)
+            for (int l = l0 + warp; l < ncol; l += kHhW) {
+                const int j = l * C + c;
+                z_t *col = Bl + hh_base<C>(n, c, l);
+                const z_t vj = s_v[j - b0], qj = s_q[j - b0];
+                for (int r = j + lane; r < n; r += 32) {
+                    const z_t vr = s_v[r - b0], qr = s_q[r - b0];
+                    z_t bb = col[r - j];
+                    bb.x -= vr.x * qj.x + vr.y * qj.y + qr.x * vj.x + qr.y * vj.y;
+                    bb.y -= vr.y * qj.x - vr.x * qj.y + qr.y * vj.x - qr.x * vj.y;
+                    if (r == j) bb.y = 0.0;
+                    col[r - j] = bb;
+                }
+            }
+            __syncthreads();
+        }
+        if (k + 2 < n && c == (k + 1) % C) house(k + 1);
+    }
+    for (int l = tid; l < ncol; l += kHhT) w.d[l * C + c] = Bl[hh_base<C>(n, c, l)].x;
+    __threadfence();
+    cl.sync();
+    if (c == 0) {
+        for (int k = tid; k < n; k += kHhT) w.e[k] = (k + 1 < n) ? sqrt(zabs2(__ldcg(&w.esub[k]))) : 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            w.delta[0] = zmk(1.0, 0.0);
+            for (int k = 0; k + 1 < n; k++) {
+                const double ae = w.e[k];
+                w.delta[k + 1] = (ae > 0.0) ? zmul(w.delta[k], zscale(__ldcg(&w.esub[k]), 1.0 / ae)) : w.delta[k];
+            }
+        }
+    }
+}
+
+template <int C>
+size_t hh_dyn_bytes(int n) { return (size_t)hh_base<C>(n, 0, hh_cols<C>(n, 0)) * sizeof(z_t); }
+
+// Launches the clustered reduction with C CTAs if the cluster fits (shared
+// memory, co-residency); returns cudaErrorNotSupported when it does not.
+template <int C>
+cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cudaStream_t st) {
+    static int state = 0;          // 0 unknown, 1 usable, 2 not usable
+    static size_t set_bytes = 0;
+    constexpr size_t kStatic = (size_t)(5 * kMaxN + kHhMaxCols + 1) * sizeof(z_t) + 64 * sizeof(double);
+    const size_t bytes = hh_dyn_bytes<C>(n);
+    if (state == 2 || bytes + kStatic > 227 * 1024) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kHhT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (bytes > set_bytes) {
+        if (C > 8 && cudaFuncSetAttribute(k_heev_reduce_cl<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess) {
+            cudaGetLastError();
+            state = 2;
+            return cudaErrorNotSupported;
+        }
+        if (cudaFuncSetAttribute(k_heev_reduce_cl<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+        }
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_heev_reduce_cl<C>, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            if (C > 8) state = 2;
+            return cudaErrorNotSupported;
+        }
+        set_bytes = bytes;
+        state = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k_heev_reduce_cl<C>, n, A, lda, hw);
 }
 
 // Deflation test shared by every path: e_k is negligible next to its
@@ -860,7 +1093,13 @@ cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t l
     if (n <= 0) return cudaSuccess;
     if (n > kMaxN) return cudaErrorInvalidValue;
     const HeevWork hw = heev_layout(n, work);
-    k_heev_reduce<<<1, kST, 0, st>>>(n, A, lda, hw);
+    cudaError_t he = hh_launch<16>(n, A, lda, hw, st);
+    if (he == cudaErrorNotSupported) he = hh_launch<8>(n, A, lda, hw, st);
+    if (he == cudaErrorNotSupported) {
+        k_heev_reduce<<<1, kST, 0, st>>>(n, A, lda, hw);
+        he = cudaGetLastError();
+    }
+    if (he != cudaSuccess) return he;
     k_heev_tri<<<n, 32, 0, st>>>(n, hw);
     const dim3 tg((n + 15) / 16, (n + 15) / 16), tb(16, 16);
     k_heev_gram<<<tg, tb, 0, st>>>(n, hw);
