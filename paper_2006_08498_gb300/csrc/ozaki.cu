@@ -83,9 +83,50 @@ static_assert(CfgMixed::kSmem <= 232448 && CfgMixed::kAcc * kN <= kTmemCols, "re
 static_assert(kN % 16 == 0 && kW % 8 == 0 && kHalf % 16 == 0, "MMA N, TMA box rows, TMEM loads");
 static_assert(kBPart % 1024 == 0 && kATile % 1024 == 0, "128-byte swizzle atoms stay 1024-aligned");
 
+// rint(x 2^sh), ties to even, for a finite x with |x 2^sh| < 2^62, from the
+// bit pattern of x with integer operations only (FP64 issue is scarce on
+// this part, the integer pipes are not).  x = mant 2^ex exactly.
+__device__ __forceinline__ long long scaled_rint(double x, int sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    int ex = -1074;                                 // subnormal or zero
+    if (ef != 0) {
+        mant |= 1ull << 52;
+        ex = ef - 1075;
+    }
+    const int s = ex + sh;
+    unsigned long long q;
+    if (s >= 0) {
+        q = mant << s;
+    } else if (-s > 54) {
+        q = 0;                                      // mant < 2^53: below one half
+    } else {
+        const int r = -s;
+        q = mant >> r;
+        const unsigned long long rem = mant & ((1ull << r) - 1), half = 1ull << (r - 1);
+        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// Largest |re| or |im| of a line as a bit pattern: for non-negative doubles
+// the integer order of the patterns is the numeric order, and any Inf or NaN
+// compares above kNonFinite.
+constexpr unsigned long long kNonFinite = 0x7FF0000000000000ull;
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// frexp exponent of the value with pattern mb (finite, non-zero)
+__device__ __forceinline__ int frexp_bits(unsigned long long mb) {
+    int e;
+    frexp(__longlong_as_double((long long)mb), &e);
+    return e;
+}
+
 __device__ __forceinline__ void split_digits(double x, int E, int *t) {
-    // X = rint(x 2^(48 - E)), |X| <= 2^48; balanced base-256 digits
-    long long X = __double2ll_rn(ldexp(x, kBeta * kS - E));
+    // X = rint(x 2^(48 - E)), |X| <= 2^48 since |x| < 2^E; balanced base-256 digits
+    long long X = scaled_rint(x, kBeta * kS - E);
 #pragma unroll
     for (int p = kS - 1; p >= 1; p--) {
         int d = (int)(X & 0xFF);
@@ -117,39 +158,29 @@ __global__ void k_row_exponent(int64_t M, int64_t K, const z_t *__restrict__ H, 
     if (i >= M) return;
     const int64_t k0 = (int64_t)blockIdx.y * cols_per_block;
     const int64_t k1 = (k0 + cols_per_block < K) ? k0 + cols_per_block : K;
-    double mx = 0.0;
-    bool finite = true;
+    unsigned long long mb = 0;
     for (int64_t k = k0; k < k1; k++) {
         const z_t h = H[i + k * ldh];
-        finite = finite && isfinite(h.x) && isfinite(h.y);
-        mx = fmax(mx, fmax(fabs(h.x), fabs(h.y)));
+        mb = max(mb, max(abs_bits(h.x), abs_bits(h.y)));
     }
-    if (!finite) set_error(sc, DEV_NONFINITE, (int)i);
-    if (mx > 0.0) {
-        int e;
-        frexp(mx, &e);
-        atomicMax(&E[i], e);
-    }
+    if (mb >= kNonFinite) set_error(sc, DEV_NONFINITE, (int)i);
+    else if (mb > 0) atomicMax(&E[i], frexp_bits(mb));
 }
 
 __global__ void k_col_exponent(int64_t N, int n, const z_t *__restrict__ Y, int64_t ldy, int *F,
                                ChaseScalars *sc) {
     const int j = blockIdx.y;
     if (j >= n) return;
-    double mx = 0.0;
-    bool finite = true;
+    unsigned long long mb = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
          k += (int64_t)gridDim.x * blockDim.x) {
         const z_t y = Y[k + j * ldy];
-        finite = finite && isfinite(y.x) && isfinite(y.y);
-        mx = fmax(mx, fmax(fabs(y.x), fabs(y.y)));
+        mb = max(mb, max(abs_bits(y.x), abs_bits(y.y)));
     }
-    if (!finite) set_error(sc, DEV_NONFINITE, j);
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx > 0.0) {
-        int e;
-        frexp(mx, &e);
-        atomicMax(&F[j], e);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if ((threadIdx.x & 31) == 0) {
+        if (mb >= kNonFinite) set_error(sc, DEV_NONFINITE, j);
+        else if (mb > 0) atomicMax(&F[j], frexp_bits(mb));
     }
 }
 
