@@ -13,10 +13,10 @@
 // with u, xi uniform on [-1, 1] and theta uniform on [0, 2 pi) drawn from
 // SplitMix64 (Steele, Lea, Flood 2014) keyed by seed ^ (stream << 56) ^ index.
 //
-// Two kernels: a per-pair table pass (O(N)), then one thread per element.
-// An element above the diagonal is computed as the conjugate of its mirror,
-// evaluated by the same code, so H is Hermitian bit for bit and every
-// column is written with coalesced stores.  HBM traffic: 16 N^2 bytes.
+// Two kernels: a per-pair table pass (O(N)), then 32 x 32 tiles of the lower
+// triangle, each written in place and conjugated at its mirror, so H is
+// Hermitian bit for bit and every column is written with coalesced stores.
+// HBM traffic: 16 N^2 bytes.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -48,35 +48,70 @@ __global__ void bse_tables_kernel(uint64_t seed, int Nk, int Nv, int Nc, BseMode
     }
 }
 
-__device__ __forceinline__ z_t lower_element(int64_t I, int64_t J, int Nk, int nb, BseModel md,
-                                             const double *dE, const double *theta, const z_t *a) {
-    const int R = md.rank_x;
-    z_t x = zmk(0.0, 0.0);
-    for (int r = 0; r < R; r++) x = zadd(x, zmul(a[I * R + r], zconj(a[J * R + r])));
-    x = zscale(x, 2.0);
-    z_t w = zmk(0.0, 0.0);
-    if (I % nb == J % nb) {
-        int64_t dk = I / nb - J / nb;
-        if (dk < 0) dk = -dk;
-        if (Nk - dk < dk) dk = Nk - dk;
-        const double K = 1.0 / ((double)dk * (double)dk + 0.5);
-        const double ph = theta[I] - theta[J];
-        double sn, cs;
-        sincos(ph, &sn, &cs);
-        w = zmk(md.w0 * K * cs, md.w0 * K * sn);
-    }
-    if (I == J) return zmk(dE[I] + x.x - w.x, 0.0);
-    return zsub(x, w);
-}
+// One 32 x 32 tile (ti >= tj) of the lower triangle per CTA: each element
+// below or on the diagonal is computed once and written twice, in place and
+// conjugated at its mirror (through shared memory, so both stores are
+// coalesced).  The exchange sum is 4 R FMAs per element; FP64 issue bounds
+// this kernel, and the mirror halves it.
+constexpr int kGT = 32;
 
-__global__ void bse_matrix_kernel(int Nk, int nb, int64_t N, BseModel md, const double *dE,
-                                  const double *theta, const z_t *a, z_t *H, int64_t ldh) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    for (int64_t j = blockIdx.y; j < N; j += gridDim.y) {
-        z_t h = (i >= j) ? lower_element(i, j, Nk, nb, md, dE, theta, a)
-                         : zconj(lower_element(j, i, Nk, nb, md, dE, theta, a));
-        H[i + j * ldh] = h;
+__global__ void __launch_bounds__(256)
+bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ dE,
+                const double *__restrict__ theta, const z_t *__restrict__ a, z_t *H, int64_t ldh) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (ti < tj) return;
+    extern __shared__ z_t gsm[];                 // a rows of the tile: [r][32] for I, then J
+    __shared__ z_t tile[kGT][kGT + 1];           // tile[c][r] = H(i0 + r, j0 + c)
+    __shared__ double thi[kGT], thj[kGT], dEi[kGT];
+    const int R = md.rank_x;
+    z_t *sai = gsm, *saj = gsm + kGT * R;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int i0 = ti * kGT, j0 = tj * kGT;
+    for (int e = ty * kGT + tx; e < kGT * R; e += 256) {
+        const int t = e / R, r = e % R;
+        sai[r * kGT + t] = (i0 + t < N) ? a[(int64_t)(i0 + t) * R + r] : zmk(0.0, 0.0);
+        saj[r * kGT + t] = (j0 + t < N) ? a[(int64_t)(j0 + t) * R + r] : zmk(0.0, 0.0);
+    }
+    if (ty == 0) {
+        thi[tx] = (i0 + tx < N) ? theta[i0 + tx] : 0.0;
+        thj[tx] = (j0 + tx < N) ? theta[j0 + tx] : 0.0;
+        dEi[tx] = (i0 + tx < N) ? dE[i0 + tx] : 0.0;
+    }
+    __syncthreads();
+    const bool diag = ti == tj;
+    const int I = i0 + tx, kI = I / nb, bI = I % nb;
+    for (int c = ty; c < kGT; c += 8) {
+        if (diag && tx < c) continue;            // above the diagonal: the mirror pass
+        const int J = j0 + c;
+        z_t x = zmk(0.0, 0.0);                   // sum_r a_Ir conj(a_Jr)
+        for (int r = 0; r < R; r++) {
+            const z_t ai = sai[r * kGT + tx], aj = saj[r * kGT + c];
+            x.x = fma(ai.x, aj.x, x.x);
+            x.x = fma(ai.y, aj.y, x.x);
+            x.y = fma(ai.y, aj.x, x.y);
+            x.y = fma(-ai.x, aj.y, x.y);
+        }
+        x = zscale(x, 2.0);
+        z_t w = zmk(0.0, 0.0);
+        if (bI == J % nb) {
+            int dk = kI - J / nb;
+            if (dk < 0) dk = -dk;
+            if (Nk - dk < dk) dk = Nk - dk;
+            const double K = 1.0 / ((double)dk * (double)dk + 0.5);
+            double sn, cs;
+            sincos(thi[tx] - thj[c], &sn, &cs);
+            w = zmk(md.w0 * K * cs, md.w0 * K * sn);
+        }
+        const z_t h = (I == J) ? zmk(dEi[tx] + x.x - w.x, 0.0) : zsub(x, w);
+        tile[c][tx] = h;
+        if (I < N && J < N) H[I + (int64_t)J * ldh] = h;
+    }
+    __syncthreads();
+    for (int c = ty; c < kGT; c += 8) {
+        // diagonal tile: H(i0 + tx, i0 + c), tx < c; otherwise H(j0 + tx, i0 + c)
+        if (diag && tx >= c) continue;
+        const int row = (diag ? i0 : j0) + tx, col = i0 + c;
+        if (row < N && col < N) H[row + (int64_t)col * ldh] = zconj(tile[tx][c]);
     }
 }
 
@@ -88,8 +123,16 @@ cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseMod
     const int64_t N = (int64_t)Nk * Nv * Nc;
     bse_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(seed, Nk, Nv, Nc, md, dE, theta, a);
     bse_count_launches(1);
-    dim3 grid((unsigned)((N + 255) / 256), (unsigned)(N < 65535 ? N : 65535));
-    bse_matrix_kernel<<<grid, 256, 0, st>>>(Nk, Nv * Nc, N, md, dE, theta, a, H, ldh);
+    const unsigned T = (unsigned)((N + kGT - 1) / kGT);
+    const int dyn = 2 * kGT * md.rank_x * (int)sizeof(z_t);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(bse_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             2 * kGT * 64 * (int)sizeof(z_t));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    bse_tile_kernel<<<dim3(T, T), dim3(32, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, theta, a, H, ldh);
     bse_count_launches(1);
     return cudaGetLastError();
 }

@@ -284,6 +284,16 @@ def test_rayleigh_ritz_full_space_degenerate(ctx, n):
 
 # ---------------------------------------------------------------- solve
 
+# Ritz values agree with the oracle's ChASE run to rtol EVAL_RTOL[precision].
+# Through the tensor-core products every operand carries 48 bits relative to
+# its row / column maximum, so one Gram entry q_i^H (H q_j) is exact to about
+# sqrt(K) 2^-48 max|q_i| max|H q_j| (K = N) rather than to 2^-53 of its size;
+# on the N = 2000 cases that is 0.6e-12 .. 1.9e-12 relative in the Ritz
+# values (the native FP64 path: 5e-15).  Both stay within 1e-10 of the dense
+# eigenvalues, which _check_solution asserts.
+EVAL_RTOL = {pkg.CHASE_FP64: 1e-11, pkg.CHASE_FP64_DFMA: 1e-12}
+
+
 def _check_solution(H, evals, V, resid, nev, w_exact=None, ref=None):
     normH = np.max(np.abs(np.linalg.eigvalsh(H))) if w_exact is None else np.max(np.abs(w_exact))
     assert np.all(np.diff(evals) >= 0)
@@ -320,7 +330,7 @@ def test_solve_c1_matches_oracle(ctx, c1, precision):
     V = host(Vd)
     _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
     assert np.max(resid) <= 1e-10
-    assert np.allclose(evals, ref["evals"], rtol=1e-12, atol=0)
+    assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[precision], atol=0)
     assert abs(st["iters"] - ref["iters"]) <= 1
     assert st["iters"] >= 2
 
@@ -479,7 +489,7 @@ def test_solve_grouped_degrees_matches_oracle(ctx, c1):
     evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, degree_group=48)
     _check_solution(H, evals, host(Vd), resid, 50, w_exact=w, ref=ref["evecs"])
     assert np.max(resid) <= 1e-10
-    assert np.allclose(evals, ref["evals"], rtol=1e-12, atol=0)
+    assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[pkg.CHASE_FP64], atol=0)
     assert abs(st["iters"] - ref["iters"]) <= 1
     with pytest.raises(pkg.BseError):
         ctx.solve(Hd, 50, 25, degree_group=-1)
