@@ -752,11 +752,13 @@ int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int 
     if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
     DeviceGuard g(ctx->device);
     int rc;
-    const size_t tb = (size_t)N * (2 * sizeof(double) + std::max(md.rank_x, 1) * sizeof(z_t));
+    // u[N] and a[N R] first (16-byte aligned), then dE[N] and Kt[Nk/2 + 1]
+    const size_t tb = (size_t)N * (1 + std::max(md.rank_x, 1)) * sizeof(z_t) +
+                      ((size_t)N + Nk / 2 + 1) * sizeof(double);
     if ((rc = ensure(ctx, ctx->tables, tb))) return rc;
-    double *dE = (double *)ctx->tables.p, *theta = dE + N;
-    z_t *a = (z_t *)(theta + N);
-    CK(launch_bse_build(seed, Nk, Nv, Nc, md, dE, theta, a, (z_t *)d_H, ldh, ctx->st));
+    z_t *u = (z_t *)ctx->tables.p, *a = u + N;
+    double *dE = (double *)(a + N * std::max(md.rank_x, 1)), *Kt = dE + N;
+    CK(launch_bse_build(seed, Nk, Nv, Nc, md, dE, u, a, Kt, (z_t *)d_H, ldh, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return BSE_OK;
 }

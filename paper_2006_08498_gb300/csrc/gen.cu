@@ -24,11 +24,14 @@ namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-// tables: dE[N], theta[N], a[N*R] (pair-major: a[I*R + r])
+// tables: dE[N], u[N] = e^{i theta_I}, a[N*R] (pair-major: a[I*R + r]) and
+// the direct-term kernel Kt[d] = 1 / (d^2 + 1/2), d = 0 .. Nk/2, so the
+// element pass needs no transcendental: e^{i(theta_I - theta_J)} = u_I conj(u_J)
 __global__ void bse_tables_kernel(uint64_t seed, int Nk, int Nv, int Nc, BseModel md,
-                                  double *dE, double *theta, z_t *a) {
+                                  double *dE, z_t *u, z_t *a, double *Kt) {
     const int64_t N = (int64_t)Nk * Nv * Nc;
     const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (I <= Nk / 2) Kt[I] = 1.0 / ((double)I * (double)I + 0.5);
     if (I >= N) return;
     const int c = (int)(I % Nc);
     const int v = (int)((I / Nc) % Nv);
@@ -38,7 +41,9 @@ __global__ void bse_tables_kernel(uint64_t seed, int Nk, int Nv, int Nc, BseMode
     const double Ec = md.band_gap / 2.0 + c + 3.0 * md.dispersion * s + md.jitter * xi;
     const double Ev = -md.band_gap / 2.0 - 0.5 * v - 2.0 * md.dispersion * s;
     dE[I] = Ec - Ev;
-    theta[I] = kTwoPi * unif(seed, 3, (uint64_t)I);
+    double sn, cs;
+    sincos(kTwoPi * unif(seed, 3, (uint64_t)I), &sn, &cs);
+    u[I] = zmk(cs, sn);
     const double amp = sqrt(3.0 * md.x0 / (double)N) / sqrt(2.0);
     for (int r = 0; r < md.rank_x; r++) {
         const uint64_t idx = 2 * ((uint64_t)md.rank_x * I + r);
@@ -57,12 +62,14 @@ constexpr int kGT = 32;
 
 __global__ void __launch_bounds__(256)
 bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ dE,
-                const double *__restrict__ theta, const z_t *__restrict__ a, z_t *H, int64_t ldh) {
+                const z_t *__restrict__ u, const z_t *__restrict__ a, const double *__restrict__ Kt,
+                z_t *H, int64_t ldh) {
     const int ti = blockIdx.x, tj = blockIdx.y;
     if (ti < tj) return;
     extern __shared__ z_t gsm[];                 // a rows of the tile: [r][32] for I, then J
     __shared__ z_t tile[kGT][kGT + 1];           // tile[c][r] = H(i0 + r, j0 + c)
-    __shared__ double thi[kGT], thj[kGT], dEi[kGT];
+    __shared__ z_t ui[kGT], uj[kGT];
+    __shared__ double dEi[kGT];
     const int R = md.rank_x;
     z_t *sai = gsm, *saj = gsm + kGT * R;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -73,8 +80,8 @@ bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ d
         saj[r * kGT + t] = (j0 + t < N) ? a[(int64_t)(j0 + t) * R + r] : zmk(0.0, 0.0);
     }
     if (ty == 0) {
-        thi[tx] = (i0 + tx < N) ? theta[i0 + tx] : 0.0;
-        thj[tx] = (j0 + tx < N) ? theta[j0 + tx] : 0.0;
+        ui[tx] = (i0 + tx < N) ? u[i0 + tx] : zmk(0.0, 0.0);
+        uj[tx] = (j0 + tx < N) ? u[j0 + tx] : zmk(0.0, 0.0);
         dEi[tx] = (i0 + tx < N) ? dE[i0 + tx] : 0.0;
     }
     __syncthreads();
@@ -97,10 +104,7 @@ bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ d
             int dk = kI - J / nb;
             if (dk < 0) dk = -dk;
             if (Nk - dk < dk) dk = Nk - dk;
-            const double K = 1.0 / ((double)dk * (double)dk + 0.5);
-            double sn, cs;
-            sincos(thi[tx] - thj[c], &sn, &cs);
-            w = zmk(md.w0 * K * cs, md.w0 * K * sn);
+            w = zscale(zmul(ui[tx], zconj(uj[c])), md.w0 * Kt[dk]);
         }
         const z_t h = (I == J) ? zmk(dEi[tx] + x.x - w.x, 0.0) : zsub(x, w);
         tile[c][tx] = h;
@@ -118,10 +122,10 @@ bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ d
 }  // namespace
 
 cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
-                             double *dE, double *theta, z_t *a, z_t *H, int64_t ldh,
+                             double *dE, z_t *u, z_t *a, double *Kt, z_t *H, int64_t ldh,
                              cudaStream_t st) {
     const int64_t N = (int64_t)Nk * Nv * Nc;
-    bse_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(seed, Nk, Nv, Nc, md, dE, theta, a);
+    bse_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(seed, Nk, Nv, Nc, md, dE, u, a, Kt);
     bse_count_launches(1);
     const unsigned T = (unsigned)((N + kGT - 1) / kGT);
     const int dyn = 2 * kGT * md.rank_x * (int)sizeof(z_t);
@@ -132,7 +136,7 @@ cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseMod
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    bse_tile_kernel<<<dim3(T, T), dim3(32, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, theta, a, H, ldh);
+    bse_tile_kernel<<<dim3(T, T), dim3(32, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a, Kt, H, ldh);
     bse_count_launches(1);
     return cudaGetLastError();
 }

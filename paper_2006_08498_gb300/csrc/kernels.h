@@ -11,8 +11,10 @@ struct BseModel {
 };
 
 // ---- generator (gen.cu)
+// Tables (device scratch): dE[N], u[N] = e^{i theta}, a[N * rank_x] and
+// Kt[Nk / 2 + 1] = 1 / (d^2 + 1/2).
 cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
-                             double *dE, double *theta, z_t *a, z_t *H, int64_t ldh,
+                             double *dE, z_t *u, z_t *a, double *Kt, z_t *H, int64_t ldh,
                              cudaStream_t st);
 
 // ---- dense products (zgemm.cu)
@@ -134,7 +136,7 @@ cudaError_t launch_select_cols(int64_t N, int nc, const z_t *A, const z_t *B, in
 cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st);
 // X = R^{-1} for upper-triangular R (n x n)
 cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, cudaStream_t st);
-// Eigen-decomposition of Hermitian A (n x n, destroyed): ascending w, vectors Y.
+// Eigen-decomposition of Hermitian A (n x n, may be overwritten): ascending w, vectors Y.
 size_t heev_work_bytes(int n);
 cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t ldy, void *work,
                         ChaseScalars *sc, cudaStream_t st);
