@@ -55,7 +55,8 @@ constexpr int kBM = 128;           // rows per CTA
 constexpr int kW = 48;             // complex columns per CTA
 constexpr int kN = 2 * kW;         // MMA N
 constexpr int kKC = 64;            // K chunk
-constexpr int kAStages = 6;        // A stages of one part (Re or Im of one slice)
+constexpr int kAStages = 6;        // A tiles of one part (Re or Im of one slice)
+constexpr int kAPairs = kAStages / 2;  // stages of one slice (Re and Im tiles, one barrier)
 constexpr int kATile = kBM * kKC * 2;                 // 16 KB
 constexpr int kBPart = kW * kKC * 2;                  // 6 KB
 constexpr int kBSlice = 3 * kBPart;                   // [-Yi | Yr | Yi]
@@ -292,32 +293,36 @@ struct OzArgs {
     z_t *P;           // FP64 partial products of the splits [z][j][i], ld M
 };
 
-// Issue order of the TMA producer within one K chunk.  Items: A part pi
-// (pass pi = 2(p-1) + ri: slice p, ri = 0 for Re H, 1 for Im H) and B slice
-// q.  Each load first waits for its buffer to be released by an earlier
-// chunk; issuing the loads in the order of those releases (then of need)
-// keeps one late release from holding back loads that could already go.
-//   A part pi reuses the stage of part pi - kAStages (released after that
+// Issue order of the TMA producer within one K chunk.  Items: A slice p
+// (its Re and Im tiles, read by passes 2(p-1) and 2(p-1) + 1, share one stage
+// and one barrier pair) and B slice q.  Each load first waits for its buffer
+// to be released by an earlier chunk; issuing the loads in the order of
+// those releases (then of need) keeps one late release from holding back
+// loads that could already go.  Positions are counted in slices p:
+//   A slice p reuses the stage of slice p - kAPairs (released after its Im
 //   pass).  B slice q >= 2 reuses its own buffer, last read in the previous
-//   chunk by the Im pass of p = S + 1 - q (pass 2(S - q) + 1).  B slice 1
-//   alternates between two buffers; its buffer was last read by the final
-//   pass of the chunk before the previous one.
+//   chunk by the Im pass of p = S + 1 - q.  B slice 1 alternates between two
+//   buffers; its buffer was last read by the final pass of the chunk before
+//   the previous one.
+// One barrier wait and one release per slice instead of per pass: every
+// mbarrier operation the MMA thread issues between MMAs costs tensor issue
+// time.
 template <int S>
 struct ProducerOrder {
-    int kind[3 * S] = {};   // 0: A part, 1: B slice
-    int idx[3 * S] = {};    // pass pi, or slice q
+    int kind[2 * S] = {};   // 0: A slice, 1: B slice
+    int idx[2 * S] = {};    // slice p - 1, or slice q
     __host__ __device__ constexpr ProducerOrder() {
-        int wt[3 * S] = {}, need[3 * S] = {};
+        int wt[2 * S] = {}, need[2 * S] = {};
         int n = 0;
-        for (int pi = 0; pi < 2 * S; pi++, n++) {
-            kind[n] = 0; idx[n] = pi; wt[n] = pi - kAStages; need[n] = 8 * pi;
+        for (int pp = 0; pp < S; pp++, n++) {
+            kind[n] = 0; idx[n] = pp; wt[n] = pp - kAPairs; need[n] = 8 * pp;
         }
         for (int q = 1; q <= S; q++, n++) {
             kind[n] = 1; idx[n] = q;
-            wt[n] = (q == 1) ? -2 * S - 1 : 1 - 2 * q;
+            wt[n] = (q == 1) ? -S - 1 : -q;
             need[n] = S - q;
         }
-        for (int i = 1; i < 3 * S; i++)       // insertion sort on (wait, need)
+        for (int i = 1; i < 2 * S; i++)       // insertion sort on (wait, need)
             for (int j = i; j > 0; j--) {
                 const bool sw = wt[j] < wt[j - 1] ||
                                 (wt[j] == wt[j - 1] && need[j] < need[j - 1]);
@@ -362,10 +367,15 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = sm;                                        // kAStages x 16 KB
+    uint8_t *sA = sm;                                        // kAPairs x (Re, Im) x 16 KB
     uint8_t *sB = sm + kAStages * kATile;                    // kNB x [-Yi | Yr | Yi]
-    __shared__ uint64_t fullA[kAStages], emptyA[kAStages], fullB[kNB], emptyB[kNB];
-    __shared__ uint64_t accFull[kNEx], accEmpty[kNEx], tailFull, tailEmpty;
+    // fullB[gc & 1]: all S B slices of chunk gc have landed (S arrivals); the
+    // two barriers alternate so that slice 1 of the next chunk, whose buffer
+    // frees early, never arrives on the phase of the current one
+    __shared__ uint64_t fullA[kAPairs], emptyA[kAPairs], fullB[2], emptyB[kNB];
+    // accEmpty: every exact accumulator of the chunk has been read (the drain
+    // warps read them in the order g = 2, ..., kEx and arrive after the last)
+    __shared__ uint64_t accFull[kNEx], accEmpty, tailFull, tailEmpty;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -374,9 +384,11 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const int units = args.tx * args.ty * args.tz;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kAStages; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
-        for (int s = 0; s < kNB; s++) { tc::mbar_init(&fullB[s], 1); tc::mbar_init(&emptyB[s], 1); }
-        for (int s = 0; s < kNEx; s++) { tc::mbar_init(&accFull[s], 1); tc::mbar_init(&accEmpty[s], kDrainWarps); }
+        for (int s = 0; s < kAPairs; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
+        for (int s = 0; s < kNB; s++) tc::mbar_init(&emptyB[s], 1);
+        for (int s = 0; s < 2; s++) tc::mbar_init(&fullB[s], S);
+        for (int s = 0; s < kNEx; s++) tc::mbar_init(&accFull[s], 1);
+        tc::mbar_init(&accEmpty, kDrainWarps);
         tc::mbar_init(&tailFull, 1);
         tc::mbar_init(&tailEmpty, kDrainWarps);
         abort_flag = 0;
@@ -416,24 +428,28 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 unit(u, j0, i0, z, c0, c1);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
 #pragma unroll
-                    for (int it = 0; it < 3 * S; it++) {
+                    for (int it = 0; it < 2 * S; it++) {
                         if (order.kind[it] == 0) {
-                            const int pi = order.idx[it];
-                            const int ua = S2 * gc + pi, st = ua % kAStages, n = ua / kAStages;
+                            const int pp = order.idx[it];
+                            const int ua = S * gc + pp, st = ua % kAPairs, n = ua / kAPairs;
                             if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                            tc::mbar_expect_tx(&fullA[st], kATile);
-                            // part (slice p, re/im) = pi in the A tensor's part order
-                            tc::tma_load_3d(sA + st * kATile, &tmA, 0, (int)i0, pi * nch + c, &fullA[st]);
+                            tc::mbar_expect_tx(&fullA[st], 2 * kATile);
+                            // parts (slice p, re) and (slice p, im) = 2 pp, 2 pp + 1 in the
+                            // A tensor's part order
+                            uint8_t *adst = sA + st * 2 * kATile;
+                            tc::tma_load_3d(adst, &tmA, 0, (int)i0, (2 * pp) * nch + c, &fullA[st]);
+                            tc::tma_load_3d(adst + kATile, &tmA, 0, (int)i0, (2 * pp + 1) * nch + c, &fullA[st]);
                         } else {
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
                             if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                            tc::mbar_expect_tx(&fullB[b], kBSlice);
+                            uint64_t *fb = &fullB[gc & 1];
+                            tc::mbar_expect_tx(fb, kBSlice);
                             uint8_t *bdst = sB + b * kBSlice;
                             // smem [-Yi | Yr | Yi] from parts 2, 0, 1
-                            tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, &fullB[b]);
-                            tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, &fullB[b]);
-                            tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, &fullB[b]);
+                            tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, fb);
+                            tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, fb);
+                            tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, fb);
                         }
                     }
                 }
@@ -443,6 +459,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, kN);
+            // descriptors of the first A stage and B buffer; the others are
+            // offsets in 16-byte units of the 14-bit address field (the whole
+            // operand area lies below 256 KB, so no carry leaves the field)
+            const uint64_t adesc0 = tc::sdesc_sw128(sA), bdesc0 = tc::sdesc_sw128(sB);
             bool ok = true;
             int gc = 0, uc = 0;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
@@ -454,54 +474,65 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                     for (int pi = 0; pi < S2; pi++) {
                         const int p = pi / 2 + 1, ri = pi & 1;
-                        const int ua = S2 * gc + pi, st = ua % kAStages;
-                        if (!tc::mbar_wait(&fullA[st], (ua / kAStages) & 1, &abort_flag)) { ok = false; break; }
-                        tc::fence_after();
-                        const uint64_t a0 = tc::sdesc_sw128(sA + st * kATile);
+                        const int ua = S * gc + (p - 1), st = ua % kAPairs;
+                        if (ri == 0) {
+                            if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag)) { ok = false; break; }
+                            tc::fence_after();
+                        }
+                        const uint64_t a0 = adesc0 + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
+                        // One MMA: K step kk of slice pair (p, q).
+                        auto step = [&](int kk, int q) -> bool {
+                            const int g = p + q;
+                            const int b = bbuf(q, gc);
+                            if (pi == 0 && kk == 0) {
+                                // every B slice of the chunk, before its first MMA
+                                if (q == S && !tc::mbar_wait(&fullB[gc & 1], (gc >> 1) & 1, &abort_flag))
+                                    return false;
+                                // every exact accumulator of the previous chunk has been
+                                // read: one wait, before the first of them (g = kEx)
+                                if (g == kEx && gc >= 1 &&
+                                    !tc::mbar_wait(&accEmpty, (gc - 1) & 1, &abort_flag)) return false;
+                                // the tail of the previous unit must have been read
+                                if (g > kEx && first && q == S && uc >= 1 &&
+                                    !tc::mbar_wait(&tailEmpty, (uc - 1) & 1, &abort_flag)) return false;
+                                tc::fence_after();
+                            }
+                            const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
+                            // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
+                            const uint64_t b0 =
+                                bdesc0 + (uint64_t)((b * kBSlice + (ri == 0 ? kBPart : 0)) >> 4);
+                            // a fresh sum: every exact diagonal at its first pair
+                            // of the chunk, the tail at its first pair of the unit
+                            const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
+                                                          : (first && pi == 0 && q == S);
+                            const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
+                            const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
+                            if (pi == 0 || p == S)
+                                tc::mma_bf16(d, a, bd, idesc, acc);
+                            else if (q == S + 1 - p)
+                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                            else if (q == 1)
+                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                            else
+                                tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
+                            return true;
+                        };
                         // kk outer, q inner: the MMAs of one K step share their A
                         // tile, read from shared memory once into the collector
-                        // buffer and reused for every slice q of Y
+                        // buffer and reused for every slice q of Y (not in the
+                        // chunk's first pass, whose MMAs wait for each B slice and
+                        // accumulator at its first use, nor for a single pair)
 #pragma unroll
                         for (int kk = 0; kk < kKC / 16; kk++) {
 #pragma unroll
                             for (int q = S + 1 - p; q >= 1; q--) {
-                                const int g = p + q;
-                                const int b = bbuf(q, gc);
-                                if (pi == 0 && kk == 0) {
-                                    if (!tc::mbar_wait(&fullB[b], buse(q, gc) & 1, &abort_flag)) { ok = false; break; }
-                                    if (g <= kEx && gc >= 1 &&
-                                        !tc::mbar_wait(&accEmpty[g - 2], (gc - 1) & 1, &abort_flag)) { ok = false; break; }
-                                    // the tail of the previous unit must have been read
-                                    if (g > kEx && first && q == S && uc >= 1 &&
-                                        !tc::mbar_wait(&tailEmpty, (uc - 1) & 1, &abort_flag)) { ok = false; break; }
-                                    tc::fence_after();
-                                }
-                                const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
-                                const uint8_t *bq = sB + b * kBSlice;
-                                // Re pass: [Yr | Yi] (parts 1, 2); Im pass: [-Yi | Yr] (parts 0, 1)
-                                const uint64_t b0 = tc::sdesc_sw128(bq + (ri == 0 ? kBPart : 0));
-                                // a fresh sum: every exact diagonal at its first pair
-                                // of the chunk, the tail at its first pair of the unit
-                                const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
-                                                              : (first && pi == 0 && q == S);
-                                const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
-                                const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
-                                // no collector in the chunk's first pass, whose MMAs
-                                // wait on barriers between them, nor for a single pair
-                                if (pi == 0 || p == S)
-                                    tc::mma_bf16(d, a, bd, idesc, acc);
-                                else if (q == S + 1 - p)
-                                    tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
-                                else if (q == 1)
-                                    tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
-                                else
-                                    tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
+                                if (!step(kk, q)) { ok = false; break; }   // fails only in a wait
                             }
                             if (!ok) break;
                         }
                         if (!ok) break;
-                        tc::mma_commit(&emptyA[st]);
                         if (ri == 1) {
+                            tc::mma_commit(&emptyA[st]);
                             // last reader of B slice S + 1 - p; last pair of diagonal p + 1
                             const int qd = S + 1 - p;
                             tc::mma_commit(&emptyB[bbuf(qd, gc)]);
@@ -529,7 +560,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
             for (int j = 0; j < kHalf; j++) Sx[j] = 0;
             for (int c = c0; c < c1 && ok; c++, gc++) {
-#pragma unroll
+#pragma unroll 1
                 for (int g = 2; g <= kEx; g++) {
                     if (!tc::mbar_wait(&accFull[g - 2], gc & 1, &abort_flag)) { ok = false; break; }
                     tc::fence_after();
@@ -550,7 +581,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     }
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&accEmpty[g - 2]);
+                    if (lane == 0 && g == kEx) tc::mbar_arrive(&accEmpty);
                 }
             }
             uint32_t T[kHalf];           // FP32 bits of the tail
