@@ -293,6 +293,32 @@ struct OzArgs {
     z_t *P;           // FP64 partial products of the splits [z][j][i], ld M
 };
 
+// Exact diagonal g sums, per chunk, 2 kKC products (a Re and an Im MMA per
+// K step) of each slice pair (p, g - p), in units of its own weight.  A digit
+// of slice 1 is at most 2^8 in magnitude (|x| < 2^E, 48 bits: the leading
+// digit carries the rounding), the others at most 2^7.  FP32 holds every
+// integer up to 2^24 exactly, so the tensor core may sum drain_period(g)
+// chunks before the drain warps move the accumulator into the 64-bit sums.
+// The periods divide one another and the last diagonal (g = kEx) drains
+// every chunk, last.
+__host__ __device__ constexpr long long pair_bound(int p, int q) {
+    return (long long)(p == 1 ? 256 : 128) * (q == 1 ? 256 : 128);
+}
+__host__ __device__ constexpr long long diag_bound(int g) {   // per chunk
+    long long b = 0;
+    for (int p = 1; p < g; p++) b += pair_bound(p, g - p);
+    return 2 * kKC * b;
+}
+__host__ __device__ constexpr int drain_period(int g) { return g <= 3 ? 2 : 1; }
+static_assert(drain_period(2) * diag_bound(2) <= (1ll << 24) && drain_period(3) * diag_bound(3) <= (1ll << 24) &&
+                  drain_period(4) * diag_bound(4) <= (1ll << 24) && drain_period(5) * diag_bound(5) <= (1ll << 24),
+              "exact FP32 sums of the exact diagonals");
+static_assert(drain_period(5) == 1, "the last exact diagonal drains every chunk");
+// Diagonal g is drained after chunk cl (0-based within a unit of nc chunks).
+__host__ __device__ __forceinline__ bool drain_due(int g, int cl, int nc) {
+    return (cl + 1) % drain_period(g) == 0 || cl + 1 == nc;
+}
+
 // Issue order of the TMA producer within one K chunk.  Items: A slice p
 // (its Re and Im tiles, read by passes 2(p-1) and 2(p-1) + 1, share one stage
 // and one barrier pair) and B slice q.  Each load first waits for its buffer
@@ -471,6 +497,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 unit(u, j0, i0, z, c0, c1);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
                     const bool first = (c == c0);
+                    const int cl = c - c0, nc = c1 - c0;
 #pragma unroll
                     for (int pi = 0; pi < S2; pi++) {
                         const int p = pi / 2 + 1, ri = pi & 1;
@@ -503,7 +530,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 bdesc0 + (uint64_t)((b * kBSlice + (ri == 0 ? kBPart : 0)) >> 4);
                             // a fresh sum: every exact diagonal at its first pair
                             // of the chunk, the tail at its first pair of the unit
-                            const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1)
+                            const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1 && cl % drain_period(g) == 0)
                                                           : (first && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
                             const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
@@ -536,7 +563,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             // last reader of B slice S + 1 - p; last pair of diagonal p + 1
                             const int qd = S + 1 - p;
                             tc::mma_commit(&emptyB[bbuf(qd, gc)]);
-                            if (p + 1 <= kEx) tc::mma_commit(&accFull[p - 1]);
+                            if (p + 1 <= kEx && drain_due(p + 1, cl, nc)) tc::mma_commit(&accFull[p - 1]);
                         }
                     }
                 }
@@ -552,6 +579,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         bool ok = true;
         int gc = 0, uc = 0;
+        int dn[kNEx] = {};                         // drains of each exact diagonal so far
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
             int j0, z, c0, c1;
             int64_t i0;
@@ -562,7 +590,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             for (int c = c0; c < c1 && ok; c++, gc++) {
 #pragma unroll 1
                 for (int g = 2; g <= kEx; g++) {
-                    if (!tc::mbar_wait(&accFull[g - 2], gc & 1, &abort_flag)) { ok = false; break; }
+                    if (!drain_due(g, c - c0, c1 - c0)) continue;
+                    if (!tc::mbar_wait(&accFull[g - 2], dn[g - 2] & 1, &abort_flag)) { ok = false; break; }
+                    dn[g - 2]++;
                     tc::fence_after();
                     const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
                     const float scale = __int_as_float((127 + kBeta * g) << 23);   // 2^(8g)
