@@ -313,7 +313,24 @@ __host__ __device__ constexpr int drain_period(int g) { return g <= 3 ? 2 : 1; }
 static_assert(drain_period(2) * diag_bound(2) <= (1ll << 24) && drain_period(3) * diag_bound(3) <= (1ll << 24) &&
                   drain_period(4) * diag_bound(4) <= (1ll << 24) && drain_period(5) * diag_bound(5) <= (1ll << 24),
               "exact FP32 sums of the exact diagonals");
-static_assert(drain_period(5) == 1, "the last exact diagonal drains every chunk");
+static_assert(drain_period(4) == 1 && drain_period(5) == 1, "the last two exact diagonals drain every chunk");
+
+// Slice order q of the chunk's first pass (Re of slice p = 1), whose MMAs
+// wait for their operands: the tail diagonals first (no drain), then g = 4
+// and g = 5 (drained last in the previous chunk), then the B slices q = 2, 1
+// (q = 2 is released last in the previous chunk, after pass (5, Im)).
+template <int S>
+struct FirstPassOrder {
+    int q[S] = {};
+    __host__ __device__ constexpr FirstPassOrder() {
+        int n = 0;
+        for (int t = S; t >= 5; t--) q[n++] = t;   // tail: g = 1 + t > 5
+        q[n++] = 3;
+        q[n++] = 4;
+        q[n++] = 2;
+        q[n++] = 1;
+    }
+};
 // Diagonal g is drained after chunk cl (0-based within a unit of nc chunks).
 __host__ __device__ __forceinline__ bool drain_due(int g, int cl, int nc) {
     return (cl + 1) % drain_period(g) == 0 || cl + 1 == nc;
@@ -388,6 +405,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     constexpr int S = Cfg::kSl;
     constexpr int S2 = 2 * S;
     constexpr int kEx = Cfg::kEx;              // diagonals 2..kEx exact
+    static_assert(kEx == 5 && S >= 4, "FirstPassOrder and the barrier groups assume kEx = 5, S >= 4");
     constexpr int kNEx = kEx - 1;              // exact accumulators
     constexpr bool kTail = Cfg::kTail;
     constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
@@ -395,13 +413,15 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = sm;                                        // kAPairs x (Re, Im) x 16 KB
     uint8_t *sB = sm + kAStages * kATile;                    // kNB x [-Yi | Yr | Yi]
-    // fullB[gc & 1]: all S B slices of chunk gc have landed (S arrivals); the
-    // two barriers alternate so that slice 1 of the next chunk, whose buffer
-    // frees early, never arrives on the phase of the current one
-    __shared__ uint64_t fullA[kAPairs], emptyA[kAPairs], fullB[2], emptyB[kNB];
-    // accEmpty: every exact accumulator of the chunk has been read (the drain
-    // warps read them in the order g = 2, ..., kEx and arrive after the last)
-    __shared__ uint64_t accFull[kNEx], accEmpty, tailFull, tailEmpty;
+    // fullB[0][gc & 1]: B slices q >= 3 of chunk gc have landed (S - 2
+    // arrivals), fullB[1][gc & 1]: slices 2 and 1.  The two barriers of a group
+    // alternate so that slice 1 of the next chunk, whose buffer frees early,
+    // never arrives on the phase of the current one.
+    __shared__ uint64_t fullA[kAPairs], emptyA[kAPairs], fullB[2][2], emptyB[kNB];
+    // accEmpty[0]: the exact accumulators g <= kEx - 1 of the chunk have been
+    // read, accEmpty[1]: g = kEx too (the drain warps read them in the order
+    // g = 2, ..., kEx)
+    __shared__ uint64_t accFull[kNEx], accEmpty[2], tailFull, tailEmpty;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -412,9 +432,13 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAPairs; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
         for (int s = 0; s < kNB; s++) tc::mbar_init(&emptyB[s], 1);
-        for (int s = 0; s < 2; s++) tc::mbar_init(&fullB[s], S);
+        for (int s = 0; s < 2; s++) {
+            tc::mbar_init(&fullB[0][s], S - 2);
+            tc::mbar_init(&fullB[1][s], 2);
+        }
         for (int s = 0; s < kNEx; s++) tc::mbar_init(&accFull[s], 1);
-        tc::mbar_init(&accEmpty, kDrainWarps);
+        tc::mbar_init(&accEmpty[0], kDrainWarps);
+        tc::mbar_init(&accEmpty[1], kDrainWarps);
         tc::mbar_init(&tailFull, 1);
         tc::mbar_init(&tailEmpty, kDrainWarps);
         abort_flag = 0;
@@ -469,7 +493,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
                             if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
-                            uint64_t *fb = &fullB[gc & 1];
+                            uint64_t *fb = &fullB[q >= 3 ? 0 : 1][gc & 1];
                             tc::mbar_expect_tx(fb, kBSlice);
                             uint8_t *bdst = sB + b * kBSlice;
                             // smem [-Yi | Yr | Yi] from parts 2, 0, 1
@@ -489,6 +513,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // offsets in 16-byte units of the 14-bit address field (the whole
             // operand area lies below 256 KB, so no carry leaves the field)
             const uint64_t adesc0 = tc::sdesc_sw128(sA), bdesc0 = tc::sdesc_sw128(sB);
+            constexpr FirstPassOrder<S> kFirst;
             bool ok = true;
             int gc = 0, uc = 0;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
@@ -512,13 +537,16 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             const int g = p + q;
                             const int b = bbuf(q, gc);
                             if (pi == 0 && kk == 0) {
-                                // every B slice of the chunk, before its first MMA
-                                if (q == S && !tc::mbar_wait(&fullB[gc & 1], (gc >> 1) & 1, &abort_flag))
+                                // B slices before the first MMA of their group (the
+                                // chunk's first MMA reads slice FirstPassOrder.q[0] >= 3)
+                                if ((q == kFirst.q[0] || q == 2) &&
+                                    !tc::mbar_wait(&fullB[q >= 3 ? 0 : 1][gc & 1], (gc >> 1) & 1, &abort_flag))
                                     return false;
-                                // every exact accumulator of the previous chunk has been
-                                // read: one wait, before the first of them (g = kEx)
-                                if (g == kEx && gc >= 1 &&
-                                    !tc::mbar_wait(&accEmpty, (gc - 1) & 1, &abort_flag)) return false;
+                                // the previous chunk's accumulators g <= kEx - 1 before
+                                // the first of them (g = kEx - 1, q = 3), g = kEx at q = 4
+                                if ((g == kEx - 1 || g == kEx) && gc >= 1 &&
+                                    !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag))
+                                    return false;
                                 // the tail of the previous unit must have been read
                                 if (g > kEx && first && q == S && uc >= 1 &&
                                     !tc::mbar_wait(&tailEmpty, (uc - 1) & 1, &abort_flag)) return false;
@@ -544,18 +572,26 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
                             return true;
                         };
-                        // kk outer, q inner: the MMAs of one K step share their A
-                        // tile, read from shared memory once into the collector
-                        // buffer and reused for every slice q of Y (not in the
-                        // chunk's first pass, whose MMAs wait for each B slice and
-                        // accumulator at its first use, nor for a single pair)
+                        if (pi == 0) {
+                            // the chunk's first pass: slice-major in FirstPassOrder,
+                            // so the operands released last in the previous chunk
+                            // are needed last (no collector: A changes every MMA)
 #pragma unroll
-                        for (int kk = 0; kk < kKC / 16; kk++) {
+                            for (int t = 0; t < S; t++) {
+                                if (!step(0, kFirst.q[t])) { ok = false; break; }   // fails only in a wait
 #pragma unroll
-                            for (int q = S + 1 - p; q >= 1; q--) {
-                                if (!step(kk, q)) { ok = false; break; }   // fails only in a wait
+                                for (int kk = 1; kk < kKC / 16; kk++) step(kk, kFirst.q[t]);
                             }
-                            if (!ok) break;
+                        } else {
+                            // kk outer, q inner: the MMAs of one K step share their A
+                            // tile, read from shared memory once into the collector
+                            // buffer and reused for every slice q of Y (not for a
+                            // single pair)
+#pragma unroll
+                            for (int kk = 0; kk < kKC / 16; kk++) {
+#pragma unroll
+                                for (int q = S + 1 - p; q >= 1; q--) step(kk, q);   // no waits
+                            }
                         }
                         if (!ok) break;
                         if (ri == 1) {
@@ -611,7 +647,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     }
                     tc::fence_before();
                     __syncwarp();
-                    if (lane == 0 && g == kEx) tc::mbar_arrive(&accEmpty);
+                    if (lane == 0 && g >= kEx - 1) tc::mbar_arrive(&accEmpty[g == kEx ? 1 : 0]);
                 }
             }
             uint32_t T[kHalf];           // FP32 bits of the tail
