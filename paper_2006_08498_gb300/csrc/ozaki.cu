@@ -344,7 +344,8 @@ __host__ __device__ __forceinline__ bool drain_due(int g, int cl, int nc) {
 // loads that could already go.  Positions are counted in slices p:
 //   A slice p reuses the stage of slice p - kAPairs (released after its Im
 //   pass).  B slice q >= 2 reuses its own buffer, last read in the previous
-//   chunk by the Im pass of p = S + 1 - q.  B slice 1 alternates between two
+//   chunk by the Im pass of p = S + 1 - q; the slices q >= S - 2 are released
+//   together after the Im pass of p = 3.  B slice 1 alternates between two
 //   buffers; its buffer was last read by the final pass of the chunk before
 //   the previous one.
 // One barrier wait and one release per slice instead of per pass: every
@@ -362,7 +363,7 @@ struct ProducerOrder {
         }
         for (int q = 1; q <= S; q++, n++) {
             kind[n] = 1; idx[n] = q;
-            wt[n] = (q == 1) ? -S - 1 : -q;
+            wt[n] = (q == 1) ? -S - 1 : (q >= S - 2) ? 2 - S : -q;
             need[n] = S - q;
         }
         for (int i = 1; i < 2 * S; i++)       // insertion sort on (wait, need)
@@ -417,7 +418,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // arrivals), fullB[1][gc & 1]: slices 2 and 1.  The two barriers of a group
     // alternate so that slice 1 of the next chunk, whose buffer frees early,
     // never arrives on the phase of the current one.
-    __shared__ uint64_t fullA[kAPairs], emptyA[kAPairs], fullB[2][2], emptyB[kNB];
+    // emptyB[b]: B buffer b may be refilled; the buffers of slices q >= S - 2
+    // (last read by the Im passes of p = 1, 2, 3) share emptyBg instead, one
+    // release after p = 3
+    __shared__ uint64_t fullA[kAPairs], emptyA[kAPairs], fullB[2][2], emptyB[kNB], emptyBg;
     // accEmpty[0]: the exact accumulators g <= kEx - 1 of the chunk have been
     // read, accEmpty[1]: g = kEx too (the drain warps read them in the order
     // g = 2, ..., kEx)
@@ -432,6 +436,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAPairs; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
         for (int s = 0; s < kNB; s++) tc::mbar_init(&emptyB[s], 1);
+        tc::mbar_init(&emptyBg, 1);
         for (int s = 0; s < 2; s++) {
             tc::mbar_init(&fullB[0][s], S - 2);
             tc::mbar_init(&fullB[1][s], 2);
@@ -492,7 +497,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         } else {
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
-                            if (n >= 1 && !tc::mbar_wait(&emptyB[b], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                            if (n >= 1 && !tc::mbar_wait(q >= S - 2 ? &emptyBg : &emptyB[b], (n - 1) & 1, &abort_flag)) {
+                                ok = false;
+                                break;
+                            }
                             uint64_t *fb = &fullB[q >= 3 ? 0 : 1][gc & 1];
                             tc::mbar_expect_tx(fb, kBSlice);
                             uint8_t *bdst = sB + b * kBSlice;
@@ -598,7 +606,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             tc::mma_commit(&emptyA[st]);
                             // last reader of B slice S + 1 - p; last pair of diagonal p + 1
                             const int qd = S + 1 - p;
-                            tc::mma_commit(&emptyB[bbuf(qd, gc)]);
+                            if (qd < S - 2) tc::mma_commit(&emptyB[bbuf(qd, gc)]);
+                            else if (p == 3) tc::mma_commit(&emptyBg);
                             if (p + 1 <= kEx && drain_due(p + 1, cl, nc)) tc::mma_commit(&accFull[p - 1]);
                         }
                     }
