@@ -561,6 +561,132 @@ cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cuda
     return cudaLaunchKernelEx(&cfg, k_heev_reduce_cl<C>, n, A, lda, hw);
 }
 
+// Cholesky G = U^H U (Sec. "QR": the Gram matrix of the filtered block) on a
+// cluster of C CTAs, right-looking: step j takes the pivot from the owner of
+// column j, forms row j of U on every CTA's own columns, publishes it, and
+// every CTA applies the rank-one update to the trailing upper triangle of
+// its columns.  The single-CTA versions are bound by FP64 issue on one SM
+// (dot products of short rows, a warp reduction each); here the work is
+// element-wise and spread over C SMs.  Column j (rows 0..j) of the upper
+// triangle lives in the shared memory of CTA j mod C.
+template <int C>
+__host__ __device__ constexpr int ch_cols(int n, int c) { return (c < n) ? (n - c + C - 1) / C : 0; }
+template <int C>
+__host__ __device__ constexpr int ch_base(int c, int l) { return C * l * (l - 1) / 2 + (c + 1) * l; }
+
+template <int C>
+__global__ void __launch_bounds__(kHhT)
+k_cholesky_cl(int n, z_t *G, int64_t ld, ChaseScalars *sc) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ z_t Uc[];                 // own columns, rows 0..j
+    __shared__ z_t s_row[kMaxN];                // row j of U on the own columns (by column)
+    __shared__ z_t s_u[kMaxN];                  // row j of U, gathered
+    const int c = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+    const int ncol = ch_cols<C>(n, c);
+    for (int l = 0; l < ncol; l++) {
+        const int j = l * C + c;
+        z_t *col = Uc + ch_base<C>(c, l);
+        for (int r = tid; r <= j; r += kHhT) col[r] = G[r + (int64_t)j * ld];
+    }
+    cl.sync();
+    for (int j = 0; j < n; j++) {
+        const int o = j % C;
+        // pivot: G(j, j) after j earlier updates, read from its owner; every
+        // CTA takes the same decision, so all leave together on a failure
+        const double d = cl.map_shared_rank(Uc, o)[ch_base<C>(o, j / C) + j].x;
+        if (!(d > 0.0)) {
+            if (c == 0 && tid == 0) set_error(sc, DEV_CHOL_FAIL, j);
+            cl.sync();                          // nobody still reads this CTA's memory
+            return;
+        }
+        const double rjj = sqrt(d), inv = 1.0 / rjj;
+        const int l0 = (j + 1 > c) ? (j + 1 - c + C - 1) / C : 0;   // own columns > j
+        for (int l = l0 + tid; l < ncol; l += kHhT) {
+            z_t *col = Uc + ch_base<C>(c, l);
+            const z_t u = zscale(col[j], inv);
+            col[j] = u;
+            s_row[l * C + c] = u;
+        }
+        cl.sync();                              // row j published, pivot read everywhere
+        if (o == c && tid == 0) Uc[ch_base<C>(c, j / C) + j] = zmk(rjj, 0.0);
+        for (int i = j + 1 + tid; i < n; i += kHhT) s_u[i] = cl.map_shared_rank(s_row, i % C)[i];
+        __syncthreads();
+        // G(i1, i2) -= conj(U(j, i1)) U(j, i2), j < i1 <= i2, own columns i2
+        for (int l = l0 + warp; l < ncol; l += kHhW) {
+            const int i2 = l * C + c;
+            z_t *col = Uc + ch_base<C>(c, l);
+            const z_t u2 = s_u[i2];
+            for (int i1 = j + 1 + lane; i1 <= i2; i1 += 32) {
+                const z_t u1 = s_u[i1];
+                z_t g = col[i1];
+                g.x -= u1.x * u2.x + u1.y * u2.y;
+                g.y -= u1.x * u2.y - u1.y * u2.x;
+                col[i1] = g;
+            }
+        }
+        cl.sync();                              // updates done; s_row free again
+    }
+    for (int l = 0; l < ncol; l++) {
+        const int j = l * C + c;
+        const z_t *col = Uc + ch_base<C>(c, l);
+        for (int r = tid; r < n; r += kHhT) G[r + (int64_t)j * ld] = (r <= j) ? col[r] : zmk(0.0, 0.0);
+    }
+}
+
+template <int C>
+size_t ch_dyn_bytes(int n) {
+    int m = 0;
+    for (int c = 0; c < C; c++) m = max(m, ch_base<C>(c, ch_cols<C>(n, c)));
+    return (size_t)m * sizeof(z_t);
+}
+
+// Launches the clustered Cholesky with C CTAs if the cluster fits;
+// cudaErrorNotSupported otherwise.
+template <int C>
+cudaError_t ch_launch(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st) {
+    static int state = 0;          // 0 unknown, 1 usable, 2 not usable
+    static size_t set_bytes = 0;
+    constexpr size_t kStatic = (size_t)(2 * kMaxN) * sizeof(z_t) + 64;
+    const size_t bytes = ch_dyn_bytes<C>(n);
+    if (state == 2 || bytes + kStatic > 227 * 1024) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kHhT);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (bytes > set_bytes || state == 0) {
+        if (C > 8 && cudaFuncSetAttribute(k_cholesky_cl<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess) {
+            cudaGetLastError();
+            state = 2;
+            return cudaErrorNotSupported;
+        }
+        if (cudaFuncSetAttribute(k_cholesky_cl<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+        }
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cholesky_cl<C>, &cfg) != cudaSuccess || nclusters < 1) {
+            cudaGetLastError();
+            if (C > 8) state = 2;
+            return cudaErrorNotSupported;
+        }
+        set_bytes = bytes > set_bytes ? bytes : set_bytes;
+        state = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, k_cholesky_cl<C>, n, G, ld, sc);
+}
+
 // Deflation test shared by every path: e_k is negligible next to its
 // diagonal neighbours.
 __device__ __forceinline__ bool tri_split(const double *d, const double *e, int k) {
@@ -1053,6 +1179,14 @@ __global__ void k_chase_update(int m_act, int nev, double tol, int deg_max,
 
 cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    if (n <= kMaxN) {
+        cudaError_t ce = ch_launch<16>(n, G, ld, sc, st);
+        if (ce == cudaErrorNotSupported) ce = ch_launch<8>(n, G, ld, sc, st);
+        if (ce != cudaErrorNotSupported) {
+            bse_count_launches(1);
+            return ce;
+        }
+    }
     if (n <= kCholSmemN) {
         const int bytes = (kCholSmemN * (kCholSmemN + 1) / 2) * (int)sizeof(z_t);
         static bool attr = false;
