@@ -62,7 +62,7 @@ size_t ozaki_partial_bytes(int64_t N, int m);
 // OZ_SUB C = D - op(A)B (D may alias C), OZ_GRAM (M = n) C = op(A)B, its
 // Hermitian part if hermitize, plus shift on the diagonal.  Workspace:
 // slices of op(A) (ozaki_gen_a_bytes) with M-long exponents E, slices of B
-// (ozaki_gen_b_bytes) with n-long exponents F, FP64 partials of n M
+// (ozaki_gen_b_bytes) with n-long exponents F, raw partials (24 bytes) of n M
 // complex values per split.
 enum { OZ_PLAIN = 0, OZ_SUB = 1, OZ_GRAM = 2 };
 struct OzGemmWork {
@@ -90,7 +90,7 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 // F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
 // low = 0: FP64 accuracy (6 slices, 21 slice pairs); low = 1: FP32-level
 // accuracy (the first four slices, 10 pairs, all exact).
-// K is split across CTAs (FP64 partials in `partials`, summed in a fixed
+// K is split across CTAs (raw int64 + FP32 partials in `partials`, summed in a fixed
 // order) when that fills the `sms` multiprocessors better.  When ev0/ev1
 // are given they are recorded on `st` just before and after the
 // tensor-core kernel itself (not the slicing or the split-K sum).

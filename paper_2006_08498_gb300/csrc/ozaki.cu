@@ -290,8 +290,18 @@ struct OzArgs {
     ChaseScalars *sc;
     int csplit;       // K chunks per split
     int tx, ty, tz;   // work units: column tiles x row tiles x splits
-    z_t *P;           // FP64 partial products of the splits [z][j][i], ld M
+    unsigned long long *P;   // raw partials of the splits, layout below
 };
+
+// Raw partial product of split z for output (i, j): per (z, j) three blocks
+// of M 8-byte words, S of the real part (int64), S of the imaginary part
+// (int64), and the FP32 tails T of both parts (float2), so that the splits
+// are summed exactly in integers before the single FP64 recombination
+// C = 2^(e_i + f_j) (S 2^-40 + T) in the reduction kernels.
+constexpr int kPartWords = 3;
+__host__ __device__ __forceinline__ int64_t part_word(int z, int n, int j, int blk, int64_t M, int64_t i) {
+    return (((int64_t)z * n + j) * kPartWords + blk) * M + i;
+}
 
 // Exact diagonal g sums, per chunk, 2 kKC products (a Re and an Im MMA per
 // K step) of each slice pair (p, g - p), in units of its own weight.  A digit
@@ -677,36 +687,19 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
             }
             if (!ok) break;
-            // Recombination C = 2^(e+f) (S 2^-40 + T) into the FP64 partial
-            // of this split (k_split_reduce sums the splits and applies the
-            // epilogue).  The column exponents of the tile come from two
-            // coalesced loads per warp and warp shuffles: one dependent
-            // global load per column, issued behind the previous column's
-            // store, cost about a microsecond each under this kernel's HBM
-            // traffic.  FP64 issue is slow on this part, so the powers of two
-            // are built from exponent bits.
+            // Raw partials of this split: S (int64) and the FP32 tail T; the
+            // reduction kernels sum the splits exactly and recombine once.
             const int jn = args.n - j0;                      // valid columns of the tile
-            const int fa = (lane < jn) ? args.F[j0 + lane] : 0;
-            const int fb = (lane + 32 < kW && lane + 32 < jn) ? args.F[j0 + 32 + lane] : 0;
             const int64_t i = i0 + row;
-            int e = (i < args.M) ? args.E[i] : 0;
-            if (e == INT_MIN) e = 0;
-            double *pbase = (double *)(args.P + ((int64_t)z * args.n + j0) * args.M + i) + half;
+            if (i < args.M) {
+                unsigned long long *P = args.P;
+                uint32_t *Pt = (uint32_t *)args.P;
 #pragma unroll
-            for (int v = 0; v < kHalf; v++) {
-                int f = (v < 32) ? __shfl_sync(0xffffffffu, fa, v) : __shfl_sync(0xffffffffu, fb, v - 32);
-                if (v >= jn) continue;
-                if (f == INT_MIN) f = 0;
-                const int x = e + f;
-                double val;
-                if (x > -960 && x < 1000) {
-                    const double sc = __longlong_as_double((long long)(1023 + x) << 52);
-                    const double sc40 = __longlong_as_double((long long)(1023 - 40 + x) << 52);
-                    val = fma((double)Sx[v], sc40, (double)__uint_as_float(T[v]) * sc);
-                } else {
-                    val = ldexp((double)Sx[v] * 0x1.0p-40 + (double)__uint_as_float(T[v]), x);
+                for (int v = 0; v < kHalf; v++) {
+                    if (v >= jn) break;
+                    P[part_word(z, args.n, j0 + v, half, args.M, i)] = (unsigned long long)Sx[v];
+                    Pt[2 * part_word(z, args.n, j0 + v, 2, args.M, i) + half] = T[v];
                 }
-                if (i < args.M) pbase[(int64_t)v * args.M * 2] = val;
             }
         }
     }
@@ -720,15 +713,39 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     }
 }
 
-// C = epi(sum over splits z of P[z]) in increasing z (deterministic).
-__global__ void k_split_reduce(int64_t M, int n, int nsplit, const z_t *__restrict__ P,
-                               GemmEpi ep, const z_t *__restrict__ Y, int64_t ldy, z_t *C,
-                               int64_t ldc) {
+// One output of the emulated product: the splits' S summed in int64 (exact)
+// and T in FP32 (the tail is below 2^-32 of the result's scale), then
+// C = 2^x (S 2^-40 + T), x = e_i + f_j.  The powers of two are built from
+// exponent bits (FP64 issue is slow on this part).
+__device__ __forceinline__ z_t recombine(const unsigned long long *__restrict__ P, int nsplit, int n,
+                                         int j, int64_t M, int64_t i, int x) {
+    long long sr = 0, si = 0;
+    float tr = 0.f, ti = 0.f;
+    for (int z = 0; z < nsplit; z++) {
+        sr += (long long)P[part_word(z, n, j, 0, M, i)];
+        si += (long long)P[part_word(z, n, j, 1, M, i)];
+        const float2 t = ((const float2 *)P)[part_word(z, n, j, 2, M, i)];
+        tr += t.x;
+        ti += t.y;
+    }
+    if (x > -960 && x < 1000) {
+        const double sc = __longlong_as_double((long long)(1023 + x) << 52);
+        const double sc40 = __longlong_as_double((long long)(1023 - 40 + x) << 52);
+        return zmk(fma((double)sr, sc40, (double)tr * sc), fma((double)si, sc40, (double)ti * sc));
+    }
+    return zmk(ldexp((double)sr * 0x1.0p-40 + (double)tr, x), ldexp((double)si * 0x1.0p-40 + (double)ti, x));
+}
+
+__device__ __forceinline__ int exp_or_zero(int e) { return e == INT_MIN ? 0 : e; }
+
+// C = epi(H Y) from the splits' partials (summed in increasing z: deterministic).
+__global__ void k_split_reduce(int64_t M, int n, int nsplit, const unsigned long long *__restrict__ P,
+                               const int *__restrict__ E, const int *__restrict__ F, GemmEpi ep,
+                               const z_t *__restrict__ Y, int64_t ldy, z_t *C, int64_t ldc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= M) return;
-    z_t v = zmk(0.0, 0.0);
-    for (int z = 0; z < nsplit; z++) v = zadd(v, P[((int64_t)z * n + j) * M + i]);
+    z_t v = recombine(P, nsplit, n, j, M, i, exp_or_zero(E[i]) + exp_or_zero(F[j]));
     if (ep.mode == GEMM_CHEB) {
         v = zscale(zsub(v, zscale(Y[i + j * ldy], ep.c)), ep.s1);
         if (ep.Yp) v = zsub(v, zscale(ep.Yp[i + j * ep.ldyp], ep.s2));
@@ -736,23 +753,22 @@ __global__ void k_split_reduce(int64_t M, int n, int nsplit, const z_t *__restri
     C[i + j * ldc] = v;
 }
 
-// General products: C = out(sum over splits z of P[z]) in increasing z.
+// General products: C = out(op(A) B) from the splits' partials.
 // OZ_PLAIN: C = S; OZ_SUB: C = D - S (D may alias C); OZ_GRAM (square):
 // C = S, or its Hermitian part (S + S^H)/2, plus shift on the diagonal.
-__global__ void k_gen_reduce(int64_t M, int n, int nsplit, const z_t *__restrict__ P, int mode,
+__global__ void k_gen_reduce(int64_t M, int n, int nsplit, const unsigned long long *__restrict__ P,
+                             const int *__restrict__ E, const int *__restrict__ F, int mode,
                              const z_t *D, int64_t ldd, double shift, int hermitize, z_t *C,
                              int64_t ldc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= M) return;
-    z_t v = zmk(0.0, 0.0);
-    for (int z = 0; z < nsplit; z++) v = zadd(v, P[((int64_t)z * n + j) * M + i]);
+    z_t v = recombine(P, nsplit, n, j, M, i, exp_or_zero(E[i]) + exp_or_zero(F[j]));
     if (mode == OZ_SUB) {
         v = zsub(D[i + j * ldd], v);
     } else if (mode == OZ_GRAM) {
         if (hermitize) {
-            z_t t = zmk(0.0, 0.0);
-            for (int z = 0; z < nsplit; z++) t = zadd(t, P[((int64_t)z * n + i) * M + j]);
+            const z_t t = recombine(P, nsplit, n, (int)i, M, j, exp_or_zero(E[j]) + exp_or_zero(F[i]));
             v = zmk(0.5 * (v.x + t.x), 0.5 * (v.y - t.y));
             if (i == j) v.y = 0.0;
         }
@@ -796,21 +812,22 @@ bool make_map(CUtensorMap *m, void *base, uint64_t rows, uint64_t tiles, uint32_
 // Split K into `sp` ranges so that the units (tiles x splits) spread
 // evenly over one persistent CTA per SM.  Cost in K-chunk units: the
 // busiest CTA's units, each with half a chunk of pipeline fill and drain,
-// plus the FP64 partials written and summed by the reduction (32 bytes per
+// plus the raw partials written and summed by the reduction (48 bytes per
 // complex output and split, at about one chunk per 6 us and 6 TB/s).  At
 // least 16 K chunks per split, partials within the workspace; 0 if even one
 // split does not fit.
 int choose_splits(int tiles, int nchunks, int n, int64_t M, size_t partial_bytes, int sms) {
-    if ((int64_t)n * M * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) return 0;
+    constexpr int64_t kPB = kPartWords * 8;       // bytes per complex output and split
+    if ((int64_t)n * M * kPB > (int64_t)partial_bytes) return 0;
     int best = 1;
     double best_t = 1e30;
     for (int sp = 1; sp <= 32; sp++) {
         if ((int64_t)sp * 16 > nchunks && sp > 1) break;
-        if ((int64_t)sp * n * M * (int64_t)sizeof(z_t) > (int64_t)partial_bytes) break;
+        if ((int64_t)sp * n * M * kPB > (int64_t)partial_bytes) break;
         const int64_t u = (int64_t)tiles * sp;
         const int64_t per = (u + sms - 1) / sms;
         const double chunks = (double)((nchunks + sp - 1) / sp);
-        const double part = (double)sp * n * M * 32.0 / (6.0e12 * 6.0e-6);
+        const double part = (double)sp * n * M * (2.0 * kPB) / (6.0e12 * 6.0e-6);
         const double t = (double)per * (chunks + 0.5) + part;
         if (t < best_t - 1e-9) { best_t = t; best = sp; }
     }
@@ -828,7 +845,7 @@ size_t ozaki_a_bytes(int64_t N) {
 
 size_t ozaki_partial_bytes(int64_t N, int m) {
     const int mp = (m + kW - 1) / kW * kW;
-    return (size_t)N * sizeof(z_t) * std::max<int64_t>(16 * kW, 8 * (int64_t)mp);
+    return (size_t)N * (kPartWords * 8) * std::max<int64_t>(16 * kW, 8 * (int64_t)mp);
 }
 
 size_t ozaki_b_bytes(int64_t N, int m) {
@@ -903,7 +920,7 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     if (best < 1) return cudaErrorInvalidValue;
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
-    a.P = partials;
+    a.P = (unsigned long long *)partials;
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
@@ -916,7 +933,7 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     if (ev1) cudaEventRecord(ev1, st);
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
-    k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, partials, ep, Y, ldy, C, ldc);
+    k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, a.P, a.E, a.F, ep, Y, ldy, C, ldc);
     bse_count_launches(1);
     return cudaGetLastError();
 }
@@ -981,7 +998,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     if (best < 1) return cudaErrorInvalidValue;
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
-    a.P = w.P;
+    a.P = (unsigned long long *)w.P;
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
@@ -989,7 +1006,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     cudaError_t e = launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((M + 255) / 256), (unsigned)n);
-    k_gen_reduce<<<gr, 256, 0, st>>>(M, n, nsplit, w.P, mode, D, ldd, shift, hermitize, C, ldc);
+    k_gen_reduce<<<gr, 256, 0, st>>>(M, n, nsplit, a.P, a.E, a.F, mode, D, ldd, shift, hermitize, C, ldc);
     bse_count_launches(1);
     return cudaGetLastError();
 }
