@@ -407,13 +407,16 @@ def run_serving(args):
     end = time.perf_counter()
     lat = np.array([r["latency"] for r in res])
     ok = sum(r["status"] == pkg.BSE_OK for r in res)
+    statuses = {}
+    for r in res:
+        statuses[str(r["status"])] = statuses.get(str(r["status"]), 0) + 1
     warm_used = sum(1 for q in reqs if q["warm"] is not None)
     ctx.server_destroy()
     ctx.close()
     line = {"metric": "chase_serving_latency_p99", "value": float(np.percentile(lat, 99)),
             "unit": "s", "higher_is_better": False, "n_gpus": 1,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "solves_per_s": n_req / (end - start), "requests": n_req, "ok": ok,
+            "solves_per_s": n_req / (end - start), "requests": n_req, "ok": ok, "statuses": statuses,
             "warm_requests": warm_used, "arrival_rate_per_s": rate,
             "calibrated_capacity_per_s": cap, "slots": args.slots, "budget_bytes": budget,
             "precision": args.precision, "degree_group": args.degree_group, "data": "synthetic",

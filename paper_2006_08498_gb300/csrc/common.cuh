@@ -7,7 +7,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #define BSE_DEV __device__ __forceinline__
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel, under
+// std::call_once: concurrent solver threads never launch before it is set.
+inline cudaError_t smem_attr_once(std::once_flag &flag, cudaError_t &status, const void *kernel,
+                                  int bytes) {
+    std::call_once(flag, [&] {
+        status = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
+    return status;
+}
+
 
 typedef double2 z_t;
 typedef float2 c_t;

@@ -877,13 +877,9 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 template <class Cfg>
 cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a,
                            dim3 grid, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_ozaki_zgemm<Cfg>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    if (smem_attr_once(once, attr, (const void *)k_ozaki_zgemm<Cfg>, Cfg::kSmem) != cudaSuccess) return attr;
     k_ozaki_zgemm<Cfg><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
     bse_count_launches(1);
     return cudaGetLastError();

@@ -15,6 +15,9 @@
 // sizes).  Failures set an error word instead of trapping.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -516,15 +519,42 @@ k_heev_reduce_cl(int n, const z_t *A, int64_t lda, HeevWork w) {
 template <int C>
 size_t hh_dyn_bytes(int n) { return (size_t)hh_base<C>(n, 0, hh_cols<C>(n, 0)) * sizeof(z_t); }
 
-// Launches the clustered reduction with C CTAs if the cluster fits (shared
-// memory, co-residency); returns cudaErrorNotSupported when it does not.
+// One-time set-up of a cluster kernel of C CTAs (called once per kernel
+// under std::call_once, so concurrent solver threads never see a half-set
+// attribute): non-portable cluster size for C > 8, the largest dynamic
+// shared memory any call may use, and a check that one such cluster fits.
+// Returns that byte limit, or 0 when the cluster form cannot run.
 template <int C>
-cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cudaStream_t st) {
-    static int state = 0;          // 0 unknown, 1 usable, 2 not usable
-    static size_t set_bytes = 0;
-    constexpr size_t kStatic = (size_t)(5 * kMaxN + kHhMaxCols + 1) * sizeof(z_t) + 64 * sizeof(double);
-    const size_t bytes = hh_dyn_bytes<C>(n);
-    if (state == 2 || bytes + kStatic > 227 * 1024) return cudaErrorNotSupported;
+size_t cluster_setup(const void *kernel, size_t max_bytes, int threads) {
+    if (C > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = max_bytes;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return max_bytes;
+}
+
+template <int C, class... Args>
+cudaError_t cluster_launch(void (*kernel)(Args...), size_t bytes, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -537,28 +567,23 @@ cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cuda
     cfg.stream = st;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (bytes > set_bytes) {
-        if (C > 8 && cudaFuncSetAttribute(k_heev_reduce_cl<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                         cudaSuccess) {
-            cudaGetLastError();
-            state = 2;
-            return cudaErrorNotSupported;
-        }
-        if (cudaFuncSetAttribute(k_heev_reduce_cl<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return cudaErrorNotSupported;
-        }
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_heev_reduce_cl<C>, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            if (C > 8) state = 2;
-            return cudaErrorNotSupported;
-        }
-        set_bytes = bytes;
-        state = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, k_heev_reduce_cl<C>, n, A, lda, hw);
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Launches the clustered reduction with C CTAs if the cluster fits (shared
+// memory, co-residency); returns cudaErrorNotSupported when it does not.
+template <int C>
+cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cudaStream_t st) {
+    constexpr size_t kStatic = (size_t)(5 * kMaxN + kHhMaxCols + 1) * sizeof(z_t) + 64 * sizeof(double);
+    static std::once_flag once;
+    static size_t limit = 0;
+    std::call_once(once, [] {
+        limit = cluster_setup<C>((const void *)k_heev_reduce_cl<C>,
+                                 std::min(hh_dyn_bytes<C>(kMaxN), (size_t)227 * 1024 - kStatic), kHhT);
+    });
+    const size_t bytes = hh_dyn_bytes<C>(n);
+    if (limit == 0 || bytes > limit) return cudaErrorNotSupported;
+    return cluster_launch<C>(k_heev_reduce_cl<C>, bytes, st, n, A, lda, hw);
 }
 
 // Cholesky G = U^H U (Sec. "QR": the Gram matrix of the filtered block) on a
@@ -646,45 +671,16 @@ size_t ch_dyn_bytes(int n) {
 // cudaErrorNotSupported otherwise.
 template <int C>
 cudaError_t ch_launch(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st) {
-    static int state = 0;          // 0 unknown, 1 usable, 2 not usable
-    static size_t set_bytes = 0;
     constexpr size_t kStatic = (size_t)(2 * kMaxN) * sizeof(z_t) + 64;
+    static std::once_flag once;
+    static size_t limit = 0;
+    std::call_once(once, [] {
+        limit = cluster_setup<C>((const void *)k_cholesky_cl<C>,
+                                 std::min(ch_dyn_bytes<C>(kMaxN), (size_t)227 * 1024 - kStatic), kHhT);
+    });
     const size_t bytes = ch_dyn_bytes<C>(n);
-    if (state == 2 || bytes + kStatic > 227 * 1024) return cudaErrorNotSupported;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(kHhT);
-    cfg.dynamicSmemBytes = bytes;
-    cfg.stream = st;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (bytes > set_bytes || state == 0) {
-        if (C > 8 && cudaFuncSetAttribute(k_cholesky_cl<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                         cudaSuccess) {
-            cudaGetLastError();
-            state = 2;
-            return cudaErrorNotSupported;
-        }
-        if (cudaFuncSetAttribute(k_cholesky_cl<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return cudaErrorNotSupported;
-        }
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_cholesky_cl<C>, &cfg) != cudaSuccess || nclusters < 1) {
-            cudaGetLastError();
-            if (C > 8) state = 2;
-            return cudaErrorNotSupported;
-        }
-        set_bytes = bytes > set_bytes ? bytes : set_bytes;
-        state = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, k_cholesky_cl<C>, n, G, ld, sc);
+    if (limit == 0 || bytes > limit) return cudaErrorNotSupported;
+    return cluster_launch<C>(k_cholesky_cl<C>, bytes, st, n, G, ld, sc);
 }
 
 // Deflation test shared by every path: e_k is negligible next to its
@@ -1189,13 +1185,9 @@ cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStr
     }
     if (n <= kCholSmemN) {
         const int bytes = (kCholSmemN * (kCholSmemN + 1) / 2) * (int)sizeof(z_t);
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        if (smem_attr_once(once, attr, (const void *)k_cholesky_smem, bytes) != cudaSuccess) return attr;
         k_cholesky_smem<<<1, kST, (size_t)(n * (n + 1) / 2) * sizeof(z_t), st>>>(n, G, ld, sc);
     } else {
         k_cholesky<<<1, kST, 0, st>>>(n, G, ld, sc);
@@ -1207,14 +1199,10 @@ cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStr
 cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t bytes = (size_t)((n + 1) & ~1) * sizeof(double) + (size_t)8 * n * sizeof(z_t);
-    static bool attr = false;
-    if (!attr) {
-        const int maxb = (int)(((kMaxN + 1) & ~1) * sizeof(double) + 8 * kMaxN * sizeof(z_t));
-        cudaError_t e = cudaFuncSetAttribute(k_trinv_cols,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    const int maxb = (int)(((kMaxN + 1) & ~1) * sizeof(double) + 8 * kMaxN * sizeof(z_t));
+    if (smem_attr_once(once, attr, (const void *)k_trinv_cols, maxb) != cudaSuccess) return attr;
     k_trinv_cols<<<(n + 7) / 8, 256, bytes, st>>>(n, R, ldr, X, ldx);
     bse_count_launches(1);
     return cudaGetLastError();
@@ -1242,13 +1230,10 @@ cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t l
     k_heev_accept<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, st>>>(n, hw);
     k_heev_chase<<<1, 32, 0, st>>>(n, hw, sc);
     const size_t zs = (size_t)32 * n * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_heev_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             32 * kMaxN * (int)sizeof(double));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    if (smem_attr_once(once, attr, (const void *)k_heev_rotate, 32 * kMaxN * (int)sizeof(double)) != cudaSuccess)
+        return attr;
     k_heev_rotate<<<(n + 31) / 32, 32, zs, st>>>(n, hw);
     k_heev_back<<<(n + 3) / 4, 128, 0, st>>>(n, hw, w, Y, ldy);
     bse_count_launches(9);

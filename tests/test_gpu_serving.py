@@ -129,3 +129,21 @@ def test_nan_request_is_reported(ctx):
     assert ctx.wait(t)["status"] == pkg.BSE_ENONFINITE
     assert ctx.wait(good)["status"] == pkg.BSE_OK                  # the server keeps serving
     ctx.server_destroy()
+
+
+def test_concurrent_mixed_sizes_all_ok(ctx):
+    """Sixteen requests of growing search-space size (m = nev + nex from 20
+    to 150) in flight on eight slots at once: every one converges.  The
+    clustered small kernels set their launch attributes once per process,
+    for the largest size, so no solver thread launches against a limit that
+    another thread is still raising."""
+    ctx.server_create(64 * GB, 8)
+    reqs = [dict(seed=100 + i, Nk=63 + 8 * (i % 5), Nv=4, Nc=4, nev=10 + 6 * i,
+                 nex=max(10, math.ceil((10 + 6 * i) / 2))) for i in range(16)]
+    tickets = [ctx.submit(**r) for r in reqs]
+    res = [ctx.wait(t) for t in tickets]
+    assert [r["status"] for r in res] == [pkg.BSE_OK] * len(reqs)
+    for r, q in zip(res, reqs):
+        assert r["nev"] == q["nev"]
+        assert np.max(r["resid"]) <= 1e-10
+    ctx.server_destroy()
