@@ -416,7 +416,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     constexpr int S = Cfg::kSl;
     constexpr int S2 = 2 * S;
     constexpr int kEx = Cfg::kEx;              // diagonals 2..kEx exact
-    static_assert(kEx == 5 && S >= 4, "FirstPassOrder and the barrier groups assume kEx = 5, S >= 4");
+    static_assert(kEx == 5 && S >= 4 && S % 2 == 0,
+                  "FirstPassOrder, its slice pairs and the barrier groups assume kEx = 5, even S >= 4");
     constexpr int kNEx = kEx - 1;              // exact accumulators
     constexpr bool kTail = Cfg::kTail;
     constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
@@ -551,7 +552,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                         const uint64_t a0 = adesc0 + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
                         // One MMA: K step kk of slice pair (p, q).
-                        auto step = [&](int kk, int q) -> bool {
+                        // coll: the A-collector use of the first pass (0: none)
+                        auto step = [&](int kk, int q, int coll) -> bool {
                             const int g = p + q;
                             const int b = bbuf(q, gc);
                             if (pi == 0 && kk == 0) {
@@ -580,7 +582,11 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                                           : (first && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
                             const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
-                            if (pi == 0 || p == S)
+                            if (pi == 0 && coll == tc::A_FILL)
+                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                            else if (pi == 0 && coll == tc::A_LASTUSE)
+                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                            else if (pi == 0 || p == S)
                                 tc::mma_bf16(d, a, bd, idesc, acc);
                             else if (q == S + 1 - p)
                                 tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
@@ -591,14 +597,22 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             return true;
                         };
                         if (pi == 0) {
-                            // the chunk's first pass: slice-major in FirstPassOrder,
-                            // so the operands released last in the previous chunk
-                            // are needed last (no collector: A changes every MMA)
+                            // the chunk's first pass in FirstPassOrder, two slices at a
+                            // time, so the operands released last in the previous
+                            // chunk are needed last; the two MMAs of one K step share
+                            // A through the collector buffer
 #pragma unroll
-                            for (int t = 0; t < S; t++) {
-                                if (!step(0, kFirst.q[t])) { ok = false; break; }   // fails only in a wait
+                            for (int t = 0; t < S; t += 2) {
+                                const int qa = kFirst.q[t], qb = kFirst.q[t + 1];
+                                if (!step(0, qa, tc::A_FILL) || !step(0, qb, tc::A_LASTUSE)) {
+                                    ok = false;   // fails only in a wait
+                                    break;
+                                }
 #pragma unroll
-                                for (int kk = 1; kk < kKC / 16; kk++) step(kk, kFirst.q[t]);
+                                for (int kk = 1; kk < kKC / 16; kk++) {
+                                    step(kk, qa, tc::A_FILL);
+                                    step(kk, qb, tc::A_LASTUSE);
+                                }
                             }
                         } else {
                             // kk outer, q inner: the MMAs of one K step share their A
@@ -608,7 +622,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                             for (int kk = 0; kk < kKC / 16; kk++) {
 #pragma unroll
-                                for (int q = S + 1 - p; q >= 1; q--) step(kk, q);   // no waits
+                                for (int q = S + 1 - p; q >= 1; q--) step(kk, q, 0);   // no waits
                             }
                         }
                         if (!ok) break;
