@@ -708,6 +708,7 @@ __device__ __forceinline__ int sturm_count(int nb, const double *d, const double
 // unreduced block that holds position j).  One warp per CTA.
 __global__ void __launch_bounds__(32) k_heev_tri(int n, HeevWork w) {
     __shared__ double sd[kMaxN], se[kMaxN], se2[kMaxN];
+    __shared__ double s_l[kMaxN], s_dp[kMaxN], s_z[kMaxN];   // twisted factorization of lane 0
     const int j = blockIdx.x, lane = threadIdx.x;
     if (j == 0 && lane == 0) *w.flag = 0;
     for (int k = lane; k < n; k += 32) {
@@ -772,53 +773,54 @@ __global__ void __launch_bounds__(32) k_heev_tri(int n, HeevWork w) {
     if (lane != 0) return;
     w.lam[j] = lam;
     // twisted factorization of T' - lam I on the block: L+ D+ L+^T from the
-    // top (multipliers in S1, pivots in S2), U- D- U-^T from the bottom,
-    // twist index r = argmin |gamma_k|
-    double *lk = w.S1, *dp = w.S2, *z = w.Z;
-    const int64_t ld = n;
+    // top (multipliers l, pivots dp), U- D- U-^T from the bottom, twist index
+    // r = argmin |gamma_k|; all in shared memory (this loop is serial, and
+    // global loads behind its own stores would each pay L2 latency)
     double piv = d[0] - lam;
     for (int k = 0; k < nb; k++) {
         if (fabs(piv) < pivmin) piv = -pivmin;
-        dp[(int64_t)(bs + k) * ld + j] = piv;
+        s_dp[k] = piv;
         if (k + 1 < nb) {
             const double ek = se[bs + k];
             const double l = ek / piv;
-            lk[(int64_t)(bs + k) * ld + j] = l;
+            s_l[k] = l;
             piv = (d[k + 1] - lam) - l * ek;
         }
     }
     double dm = d[nb - 1] - lam;
     if (fabs(dm) < pivmin) dm = -pivmin;
     int r = nb - 1;
-    double gmin = fabs(dp[(int64_t)(be - 1) * ld + j]);   // gamma_{nb-1} = dp_{nb-1}
-    // u_k (k >= 1) stored in z[k] until the vector pass overwrites it
+    double gmin = fabs(s_dp[nb - 1]);   // gamma_{nb-1} = dp_{nb-1}
+    // u_k (k >= 1) kept in s_z[k] until the vector pass overwrites it
     for (int k = nb - 2; k >= 0; k--) {
         const double ek = se[bs + k];
         const double u = ek / dm;
-        z[(int64_t)(bs + k + 1) * ld + j] = u;
+        s_z[k + 1] = u;
         dm = (d[k] - lam) - u * ek;
         if (fabs(dm) < pivmin) dm = -pivmin;
-        const double g = fabs(dp[(int64_t)(bs + k) * ld + j] + dm - (d[k] - lam));
+        const double g = fabs(s_dp[k] + dm - (d[k] - lam));
         if (g < gmin) { gmin = g; r = k; }
     }
     // z_r = 1; z_k = -l_k z_{k+1} above r, z_k = -u_k z_{k-1} below r
     double nrm = 1.0, zk = 1.0;
     for (int k = r - 1; k >= 0; k--) {
-        zk = -lk[(int64_t)(bs + k) * ld + j] * zk;
-        z[(int64_t)(bs + k) * ld + j] = zk;
+        zk = -s_l[k] * zk;
+        s_z[k] = zk;
         nrm = fma(zk, zk, nrm);
     }
-    z[(int64_t)(bs + r) * ld + j] = 1.0;
+    s_z[r] = 1.0;
     zk = 1.0;
     for (int k = r + 1; k < nb; k++) {
-        zk = -z[(int64_t)(bs + k) * ld + j] * zk;
-        z[(int64_t)(bs + k) * ld + j] = zk;
+        zk = -s_z[k] * zk;
+        s_z[k] = zk;
         nrm = fma(zk, zk, nrm);
     }
     const double inv = 1.0 / sqrt(nrm);
+    double *z = w.Z;
+    const int64_t ld = n;
     for (int k = 0; k < n; k++) {
         const int64_t ix = (int64_t)k * ld + j;
-        z[ix] = (k >= bs && k < be) ? z[ix] * inv : 0.0;
+        z[ix] = (k >= bs && k < be) ? s_z[k - bs] * inv : 0.0;
     }
 }
 
