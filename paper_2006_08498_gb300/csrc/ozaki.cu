@@ -400,15 +400,17 @@ struct ProducerOrder {
 // processed (gc) and the units (uc), and all barrier phases follow from them.
 //
 // Per K chunk the MMA warp runs 2S passes, (p, Re H) then (p, Im H) for
-// p = 1..S, and in each pass the slices q = S+1-p down to 1 of Y:
-// accumulator of diagonal g = p + q gets Re H_p x [Yr | Yi]_q (Re pass) and
-// Im H_p x [-Yi | Yr]_q (Im pass), four K=16 MMAs each.  Diagonal g's chunk
-// sum starts at pair (1, g-1) and ends at pair (g-1, 1), so the four exact
-// accumulators are drained in the order g = 2, 3, 4, 5 while later passes
-// run, and each is free again long before the next chunk reaches it.  The
-// tail (g >= EXT+1) accumulates over the unit's chunks in its own columns:
-// its weight is at most 2^-32 of the leading diagonal, so the tensor core's
+// p = 1..S, and in each pass the slices q = S+1-p down to 1 of Y (the first
+// pass in FirstPassOrder): accumulator of diagonal g = p + q gets
+// Re H_p x [Yr | Yi]_q (Re pass) and Im H_p x [-Yi | Yr]_q (Im pass), four
+// K=16 MMAs each.  Diagonal g's chunk sum starts at pair (1, g-1) and ends at
+// pair (g-1, 1), so the exact accumulators that are due (drain_due) are
+// drained in the order g = 2, 3, 4, 5 while later passes run.  The tail
+// (g >= EXT+1) accumulates over the unit's chunks in its own columns: its
+// weight is at most 2^-32 of the leading diagonal, so the tensor core's
 // truncating FP32 sums there stay far below FP64 rounding of the result.
+// The drain warps store S and the FP32 tail of each output raw; the
+// reduction kernels sum the K splits and recombine.
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
