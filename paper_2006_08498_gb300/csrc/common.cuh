@@ -11,14 +11,26 @@
 
 #define BSE_DEV __device__ __forceinline__
 
-// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel, under
-// std::call_once: concurrent solver threads never launch before it is set.
-inline cudaError_t smem_attr_once(std::once_flag &flag, cudaError_t &status, const void *kernel,
-                                  int bytes) {
-    std::call_once(flag, [&] {
-        status = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// Function attributes belong to the module loaded on each device, so the
+// one-time set-ups below are kept per device (index of the current device).
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return -1;
+    return dev;
+}
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel and
+// device, under std::call_once: concurrent solver threads never launch
+// before it is set.
+inline cudaError_t smem_attr_once(std::once_flag (&flag)[kMaxDevices], cudaError_t (&status)[kMaxDevices],
+                                  const void *kernel, int bytes) {
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorInvalidDevice;
+    std::call_once(flag[dev], [&] {
+        status[dev] = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     });
-    return status;
+    return status[dev];
 }
 
 

@@ -129,10 +129,12 @@ cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseMod
     bse_count_launches(1);
     const unsigned T = (unsigned)((N + kGT - 1) / kGT);
     const int dyn = 2 * kGT * md.rank_x * (int)sizeof(z_t);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    if (smem_attr_once(once, attr, (const void *)bse_tile_kernel, 2 * kGT * 64 * (int)sizeof(z_t)) != cudaSuccess)
-        return attr;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
+    {
+        const cudaError_t ae = smem_attr_once(once, attr, (const void *)bse_tile_kernel, 2 * kGT * 64 * (int)sizeof(z_t));
+        if (ae != cudaSuccess) return ae;
+    }
     bse_tile_kernel<<<dim3(T, T), dim3(32, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a, Kt, H, ldh);
     bse_count_launches(1);
     return cudaGetLastError();

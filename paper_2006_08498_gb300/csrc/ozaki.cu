@@ -798,16 +798,18 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// The driver's tensor-map encoder, looked up once (a thread-safe static).
 EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    static const EncodeTiledFn fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                              &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+            return (EncodeTiledFn)p;
+        cudaGetLastError();
+        return (EncodeTiledFn) nullptr;
+    }();
     return fn;
 }
 
@@ -893,9 +895,12 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 template <class Cfg>
 cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a,
                            dim3 grid, cudaStream_t st) {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    if (smem_attr_once(once, attr, (const void *)k_ozaki_zgemm<Cfg>, Cfg::kSmem) != cudaSuccess) return attr;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
+    {
+        const cudaError_t ae = smem_attr_once(once, attr, (const void *)k_ozaki_zgemm<Cfg>, Cfg::kSmem);
+        if (ae != cudaSuccess) return ae;
+    }
     k_ozaki_zgemm<Cfg><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
     bse_count_launches(1);
     return cudaGetLastError();

@@ -575,9 +575,12 @@ cudaError_t cluster_launch(void (*kernel)(Args...), size_t bytes, cudaStream_t s
 template <int C>
 cudaError_t hh_launch(int n, const z_t *A, int64_t lda, const HeevWork &hw, cudaStream_t st) {
     constexpr size_t kStatic = (size_t)(5 * kMaxN + kHhMaxCols + 1) * sizeof(z_t) + 64 * sizeof(double);
-    static std::once_flag once;
-    static size_t limit = 0;
-    std::call_once(once, [] {
+    static std::once_flag once[kMaxDevices];
+    static size_t limits[kMaxDevices];
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorNotSupported;
+    size_t &limit = limits[dev];
+    std::call_once(once[dev], [&limit] {
         limit = cluster_setup<C>((const void *)k_heev_reduce_cl<C>,
                                  std::min(hh_dyn_bytes<C>(kMaxN), (size_t)227 * 1024 - kStatic), kHhT);
     });
@@ -672,9 +675,12 @@ size_t ch_dyn_bytes(int n) {
 template <int C>
 cudaError_t ch_launch(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStream_t st) {
     constexpr size_t kStatic = (size_t)(2 * kMaxN) * sizeof(z_t) + 64;
-    static std::once_flag once;
-    static size_t limit = 0;
-    std::call_once(once, [] {
+    static std::once_flag once[kMaxDevices];
+    static size_t limits[kMaxDevices];
+    const int dev = current_device();
+    if (dev < 0) return cudaErrorNotSupported;
+    size_t &limit = limits[dev];
+    std::call_once(once[dev], [&limit] {
         limit = cluster_setup<C>((const void *)k_cholesky_cl<C>,
                                  std::min(ch_dyn_bytes<C>(kMaxN), (size_t)227 * 1024 - kStatic), kHhT);
     });
@@ -1187,9 +1193,10 @@ cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStr
     }
     if (n <= kCholSmemN) {
         const int bytes = (kCholSmemN * (kCholSmemN + 1) / 2) * (int)sizeof(z_t);
-        static std::once_flag once;
-        static cudaError_t attr = cudaSuccess;
-        if (smem_attr_once(once, attr, (const void *)k_cholesky_smem, bytes) != cudaSuccess) return attr;
+        static std::once_flag once[kMaxDevices];
+        static cudaError_t attr[kMaxDevices];
+        const cudaError_t ae = smem_attr_once(once, attr, (const void *)k_cholesky_smem, bytes);
+        if (ae != cudaSuccess) return ae;
         k_cholesky_smem<<<1, kST, (size_t)(n * (n + 1) / 2) * sizeof(z_t), st>>>(n, G, ld, sc);
     } else {
         k_cholesky<<<1, kST, 0, st>>>(n, G, ld, sc);
@@ -1201,10 +1208,13 @@ cudaError_t launch_cholesky(int n, z_t *G, int64_t ld, ChaseScalars *sc, cudaStr
 cudaError_t launch_trinv(int n, const z_t *R, int64_t ldr, z_t *X, int64_t ldx, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const size_t bytes = (size_t)((n + 1) & ~1) * sizeof(double) + (size_t)8 * n * sizeof(z_t);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
     const int maxb = (int)(((kMaxN + 1) & ~1) * sizeof(double) + 8 * kMaxN * sizeof(z_t));
-    if (smem_attr_once(once, attr, (const void *)k_trinv_cols, maxb) != cudaSuccess) return attr;
+    {
+        const cudaError_t ae = smem_attr_once(once, attr, (const void *)k_trinv_cols, maxb);
+        if (ae != cudaSuccess) return ae;
+    }
     k_trinv_cols<<<(n + 7) / 8, 256, bytes, st>>>(n, R, ldr, X, ldx);
     bse_count_launches(1);
     return cudaGetLastError();
@@ -1232,10 +1242,12 @@ cudaError_t launch_heev(int n, z_t *A, int64_t lda, double *w, z_t *Y, int64_t l
     k_heev_accept<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, st>>>(n, hw);
     k_heev_chase<<<1, 32, 0, st>>>(n, hw, sc);
     const size_t zs = (size_t)32 * n * sizeof(double);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    if (smem_attr_once(once, attr, (const void *)k_heev_rotate, 32 * kMaxN * (int)sizeof(double)) != cudaSuccess)
-        return attr;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
+    {
+        const cudaError_t ae = smem_attr_once(once, attr, (const void *)k_heev_rotate, 32 * kMaxN * (int)sizeof(double));
+        if (ae != cudaSuccess) return ae;
+    }
     k_heev_rotate<<<(n + 31) / 32, 32, zs, st>>>(n, hw);
     k_heev_back<<<(n + 3) / 4, 128, 0, st>>>(n, hw, w, Y, ldy);
     bse_count_launches(9);
