@@ -222,8 +222,11 @@ def test_filter_single_degree_closed_form(ctx, precision):
 
 # ------------------------------------------------------------------- QR
 
-@pytest.mark.parametrize("n,k,m", [(300, 0, 17), (777, 9, 33), (2000, 40, 75)])
+@pytest.mark.parametrize("n,k,m", [(300, 0, 17), (777, 9, 33), (2000, 40, 75), (2000, 0, 300),
+                                   (3000, 12, 500)])
 def test_qr_matches_oracle(ctx, n, k, m):
+    """Shifted Cholesky QR with locked projections against the oracle; m = 300
+    and 500 run the clustered Cholesky on its larger shared-memory layouts."""
     L = orthonormal(n, k, 5) if k else None
     X = block(n, m, 6)
     # moderately ill-conditioned, with a large component along the locked block
