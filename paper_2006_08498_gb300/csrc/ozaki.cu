@@ -15,12 +15,12 @@
 // split the same way per column j (exponent F_j), re and im sharing it.
 //
 // Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).
-// The diagonals g = 2..5 are accumulated in FP32 over K chunks of 64 only,
-// then drained: over one chunk the partial sums of diagonal g are integer
-// multiples of 2^(-8g) whose magnitude stays below 2^24 of those units (at
-// most 6 products of at most 2^15 per k and per real MMA), so they are
-// exact; they are converted to integers and added into one 64-bit integer
-// per output element, S = sum_g d_g 2^(8(5-g)) (|S| < 2^57 for K = 50000).
+// The diagonals g = 2..5 are accumulated in FP32 over one or two K chunks of
+// 64 only (drain_period), then drained: over that range the partial sums of
+// diagonal g are integer multiples of 2^(-8g) whose magnitude stays below
+// 2^24 of those units (diag_bound), so they are exact; they are converted to
+// integers and added into one 64-bit integer per output element,
+// S = sum_g d_g 2^(8(5-g)) (|S| < 2^57 for K = 50000).
 // Keeping these accumulations to 64 terms matters: the tensor core's FP32
 // accumulator truncates toward zero, so a sum over the whole K would carry a
 // bias growing with K.  Diagonals 6 and 7 (weight <= 2^-32 of the leading
@@ -28,18 +28,21 @@
 // at most one FP32 ulp of the running tail sum per K step of 16, i.e. below
 // (K/16) 2^-23 of the tail and about 2^-45 of the leading diagonal's scale
 // for K = 20000.  Diagonals > 7 are dropped.  The result is recombined in
-// FP64: C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij).
+// FP64, C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij), after the K splits' S and T
+// are summed (exactly, for S) by the reduction kernels.
 //
 // Complex arithmetic as two real MMAs per slice pair into one accumulator
 // of 2w columns [re | im]:  Hr x [Yr | Yi]  +  Hi x [-Yi | Yr].
 //
 // Tiling: CTA = 128 rows x 48 complex columns (MMA M = 128, N = 96), K
 // chunks of 64 (one 128-byte swizzle atom).  Warp 0 issues TMA loads, warp 1
-// issues tcgen05.mma, warps 2..9 drain the exact accumulators of every chunk
-// and run the epilogue.  TMEM holds five 96-column accumulators (480 of 512
-// columns): one per exact diagonal and the tail.  An MMA with N <= 128 costs
-// about the same issue time on this tensor core whatever N is, so the widest
-// N that leaves room for five accumulators is the one used.
+// issues tcgen05.mma, warps 2..9 drain the exact accumulators and store the
+// raw partials.  TMEM holds five 96-column accumulators (480 of 512
+// columns): one per exact diagonal and the tail.  An MMA costs a fixed ~45
+// cycles plus N/2 on this tensor core, so the widest N that leaves room for
+// five accumulators is the one used; and every instruction the single MMA
+// thread issues between MMAs (a barrier wait, a commit) costs issue time, so
+// the pipeline is built to need few of them.
 #include <algorithm>
 #include <climits>
 
