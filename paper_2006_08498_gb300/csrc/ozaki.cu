@@ -11,7 +11,7 @@
 // 2^E_i), X_ik = rint(H_ik 2^(48 - E_i)) is an integer with |X| <= 2^48,
 // written in balanced base-256 digits t_1 .. t_6 (|t_1| <= 256, |t_p| <=
 // 128 for p >= 2) so that H_ik ~ 2^E_i sum_p t_p 2^(-8p).  Slice p is stored
-// as the BF16 value t_p 2^(-8p) (exact: at most 9 significant bits).  Y is
+// as the BF16 value t_p 2^(-8p) (exact: at most 8 significant bits).  Y is
 // split the same way per column j (exponent F_j), re and im sharing it.
 //
 // Products.  Slice pair (p, q) contributes integers times 2^(-8(p+q)).
@@ -141,7 +141,7 @@ __device__ __forceinline__ void split_digits(double x, int E, int *t) {
     t[0] = (int)X;
 }
 
-// BF16 bit pattern of v; v has at most 9 significant bits, so dropping the
+// BF16 bit pattern of v; v has at most 8 significant bits, so dropping the
 // low 16 bits of its FP32 pattern is exact.
 __device__ __forceinline__ uint16_t bf16_exact(float v) {
     return (uint16_t)(__float_as_uint(v) >> 16);
