@@ -25,6 +25,11 @@
  *    return after their results are complete (host outputs written).
  *  - Every call returns a status (bse_status); no exception crosses the
  *    ABI.  bsechase_last_error() describes the last failure of a context.
+ *  - Threads: a context is used by one host thread at a time; separate
+ *    contexts (on the same or on different devices) may be used from
+ *    separate threads concurrently.  The library's one-time kernel set-up
+ *    (launch attributes, cluster checks) is done once per device under a
+ *    lock.  The request server runs its own threads, one context each.
  */
 #ifndef BSECHASE_H
 #define BSECHASE_H
