@@ -801,7 +801,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// The driver's tensor-map encoder, looked up once (a thread-safe static).
+// cuTensorMapEncodeTiled of the CUDA driver API, looked up once (a thread-safe static).
 EncodeTiledFn encode_fn() {
     static const EncodeTiledFn fn = [] {
         void *p = nullptr;
