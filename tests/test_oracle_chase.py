@@ -251,3 +251,56 @@ def test_chase_grouped_degrees_matches_dense():
     assert r["status"] == "ok" and r["iters"] <= plain["iters"]
     assert np.max(np.abs(r["evals"] - w[:40]) / np.abs(w[:40])) < 1e-10
     assert np.max(r["resid"]) <= 1e-10
+
+
+def _lanczos_closed_form(N, n_runs, seed):
+    """H = Q diag(lam) Q^H with a known spectrum, and the closed-form
+    quantities of k = N Lanczos steps from the oracle's start vectors: the
+    Ritz values of each run are the eigenvalues, and the weight of Ritz value
+    lam_i is tau_i = |q_i^H v_0|^2 (the first component of the eigenvector of
+    T is the overlap of the start vector with the eigenvector of H).  The
+    estimated count at lam_j is C_j = N * mean_runs sum_{i <= j} tau_i."""
+    r = np.random.default_rng(seed)
+    lam = np.sort(r.uniform(1.0, 9.0, N))
+    Q = np.linalg.qr(r.standard_normal((N, N)) + 1j * r.standard_normal((N, N)))[0]
+    A = (Q * lam) @ Q.conj().T
+    V0 = oracle.random_block(1, oracle.STREAM_LANCZOS, N, n_runs)
+    tau = np.abs(Q.conj().T @ (V0 / np.linalg.norm(V0, axis=0))) ** 2      # N x runs
+    C = N * np.cumsum(tau.mean(axis=1))
+    return A, lam, tau, C
+
+
+def test_lanczos_mu_m_interpolates_the_count_one_run():
+    """One run of N steps: mu_m is the point where the count N sum tau_i
+    reaches m, linear between consecutive Ritz values (closed form from the
+    eigenvectors, not from the tridiagonal), and clamps at both ends."""
+    N = 8
+    A, lam, tau, C = _lanczos_closed_form(N, 1, 2)
+    for j in range(1, N):
+        for frac in (0.2, 0.5, 0.9):
+            m = C[j - 1] + frac * (C[j] - C[j - 1])
+            want = lam[j - 1] + frac * (lam[j] - lam[j - 1])
+            est = oracle.lanczos_bounds(A, m, seed=1, n_runs=1, k_steps=N)
+            assert est["mu_m"] == pytest.approx(want, abs=1e-9)
+    assert oracle.lanczos_bounds(A, 0.5 * C[0], seed=1, n_runs=1, k_steps=N)["mu_m"] == \
+        pytest.approx(lam[0], abs=1e-9)
+    assert oracle.lanczos_bounds(A, N + 3, seed=1, n_runs=1, k_steps=N)["mu_m"] == \
+        pytest.approx(lam[-1], abs=1e-9)
+
+
+@pytest.mark.parametrize("n_runs", [2, 3])
+def test_lanczos_mu_m_pooled_runs_closed_form(n_runs):
+    """Several runs of N steps: every run's Ritz values are the eigenvalues,
+    so the pooled list holds each lam_j n_runs times, with weights
+    (N / n_runs) tau_j^(l).  A target count just below C_j (by less than the
+    smallest of those weights) is crossed inside the group of copies of lam_j,
+    so mu_m = lam_j.  A weight of N (not N / n_runs), or tau taken from the
+    last component of the eigenvector of T, moves the crossing elsewhere."""
+    N = 8
+    A, lam, tau, C = _lanczos_closed_form(N, n_runs, 2)
+    for j in range(N):
+        w = (N / n_runs) * tau[j]
+        m = C[j] - 0.5 * float(np.min(w))
+        est = oracle.lanczos_bounds(A, m, seed=1, n_runs=n_runs, k_steps=N)
+        assert est["mu_m"] == pytest.approx(lam[j], abs=1e-9)
+        assert est["mu_1"] == pytest.approx(lam[0], abs=1e-9)
