@@ -72,7 +72,16 @@ typedef enum {
                              Rayleigh-Ritz and residuals as in CHASE_FP64.
                              In single-phase entry points it selects the
                              FP32-level product.                             */
-    CHASE_FP64_DFMA = 2   /* every product in native FP64 (DFMA)            */
+    CHASE_MIXED_BF16X3 = 2, /* accepted and run as CHASE_MIXED_FP32, the
+                             closest built mode: its filter products are
+                             BF16 split products too, with four slices,
+                             because three 8-bit slices (about 24 bits per
+                             operand, products accurate to ~1e-5 relative to
+                             ||H|| ||Y|| on these matrices) cannot carry the
+                             residuals to the point where the FP64-accurate
+                             sweeps take over.  Results are bit for bit those
+                             of CHASE_MIXED_FP32.                             */
+    CHASE_FP64_DFMA = 3   /* every product in native FP64 (DFMA)            */
 } chase_precision;
 
 /* Parameters of the synthetic Eq. (1) Hamiltonian (energies in eV).

@@ -19,7 +19,7 @@ _LIBPATH = os.path.join(_HERE, "libbsechase.so")
 
 BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV = 0, -1, -2, -3
 BSE_ENONFINITE, BSE_ETIMEOUT, BSE_ECUDA, BSE_EBUSY = -4, -5, -6, -7
-CHASE_FP64, CHASE_MIXED_FP32, CHASE_FP64_DFMA = 0, 1, 2
+CHASE_FP64, CHASE_MIXED_FP32, CHASE_MIXED_BF16X3, CHASE_FP64_DFMA = 0, 1, 2, 3
 
 # Every symbol include/bsechase.h declares.
 ABI_SYMBOLS = (
@@ -198,12 +198,16 @@ def gram_noalloc(A, B, out, stream=None):
     import torch
     K, m1 = A.shape
     m2 = B.shape[1]
+    if B.device != A.device or out.device != A.device:
+        raise ValueError("A, B and out must be on one device")
     if stream is None:
         stream = torch.cuda.current_stream(A.device)
-    return load().chase_gram_noalloc(ctypes.c_void_p(A.data_ptr()), _ld(A),
-                                     ctypes.c_void_p(B.data_ptr()), _ld(B), K, m1, m2,
-                                     ctypes.c_void_p(out.data_ptr()), _ld(out),
-                                     ctypes.c_void_p(stream.cuda_stream))
+    # the entry point runs on the current device: make it A's
+    with torch.cuda.device(A.device):
+        return load().chase_gram_noalloc(ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                         ctypes.c_void_p(B.data_ptr()), _ld(B), K, m1, m2,
+                                         ctypes.c_void_p(out.data_ptr()), _ld(out),
+                                         ctypes.c_void_p(stream.cuda_stream))
 
 
 def colmajor_empty(rows, cols, device="cuda", dtype=None):

@@ -241,9 +241,20 @@ int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy
 bool precision_uses_tc(int precision) {
     return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32;
 }
+
+}  // namespace
+
 bool precision_valid(int precision) {
-    return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32 || precision == CHASE_FP64_DFMA;
+    return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32 ||
+           precision == CHASE_MIXED_BF16X3 || precision == CHASE_FP64_DFMA;
 }
+// The mode a valid precision value runs: CHASE_MIXED_BF16X3 runs as
+// CHASE_MIXED_FP32 (see the header), every other value as itself.
+int precision_mode(int precision) {
+    return precision == CHASE_MIXED_BF16X3 ? CHASE_MIXED_FP32 : precision;
+}
+
+namespace {
 
 // ---------------------------------------------------------------- phases
 
@@ -771,7 +782,8 @@ int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int 
     if (!h_evals || !d_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
     DeviceGuard g(ctx->device);
     ctx->err.clear();
-    return solve_device(ctx, (const z_t *)d_H, N, ldh, nev, nex, tol, deg_max, precision, opts,
+    return solve_device(ctx, (const z_t *)d_H, N, ldh, nev, nex, tol, deg_max,
+                        precision_mode(precision), opts,
                         h_evals, (z_t *)d_evecs, ldz, h_resid, stats);
 }
 
@@ -788,7 +800,8 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
     if ((rc = ensure(ctx, ctx->Zdev, (size_t)N * nev * sizeof(z_t)))) return rc;
     CK(cudaMemcpy2DAsync(ctx->Hdev.p, N * sizeof(z_t), h_H, ldh * sizeof(z_t), N * sizeof(z_t), N,
                          cudaMemcpyHostToDevice, ctx->st));
-    rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max, precision, opts,
+    rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max,
+                      precision_mode(precision), opts,
                       h_evals, (z_t *)ctx->Zdev.p, N, h_resid, stats);
     if (rc != BSE_OK && rc != BSE_ENOCONV) return rc;
     CK(cudaMemcpy2DAsync(h_evecs, ldz * sizeof(z_t), ctx->Zdev.p, N * sizeof(z_t), N * sizeof(z_t),
@@ -807,6 +820,7 @@ int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, in
     int rc;
     if ((rc = ensure_workspace(ctx, N, std::min<int64_t>(m, kMaxM)))) return rc;
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
            precision == CHASE_MIXED_FP32};
     if ((rc = hop_prepare(ctx, op, 8))) return rc;
@@ -835,6 +849,7 @@ int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, voi
     Small s = small_layout(ctx, m);
     CK(cudaMemcpyAsync(s.deg, h_deg, m * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
            precision == CHASE_MIXED_FP32};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
@@ -868,6 +883,7 @@ int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t l
     if ((rc = ensure_workspace(ctx, N, m))) return rc;
     Small s = small_layout(ctx, m);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
            precision == CHASE_MIXED_FP32};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
@@ -911,6 +927,7 @@ int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const
     DeviceGuard g(ctx->device);
     int rc;
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
+    precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
            precision == CHASE_MIXED_FP32};
     if ((rc = hop_prepare(ctx, op, n))) return rc;

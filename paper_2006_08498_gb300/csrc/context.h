@@ -54,6 +54,10 @@ void release_workspace(bsechase_ctx *ctx);
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
                  z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
+// Whether `precision` is a chase_precision value, and the mode it runs
+// (CHASE_MIXED_BF16X3 runs as CHASE_MIXED_FP32).
+bool precision_valid(int precision);
+int precision_mode(int precision);
 // Add the recorded tensor-core launch times to k_ms / k_flops / k_launches
 // (the stream must have been synchronised) and recycle the events.
 void harvest_kernel_times(bsechase_ctx *ctx);

@@ -55,3 +55,14 @@ def test_null_context_is_rejected(lib):
     assert lib.chase_solve(None, None, 1, 1, 1, 0, 1e-10, 36, 0, None, None, None, 1,
                            None, None) == pkg.BSE_EINVAL
     lib.bsechase_destroy(None)  # ignored
+
+
+def test_enum_values_match_binding():
+    """The status and precision values of the header are the binding's;
+    precision 2 is CHASE_MIXED_BF16X3 and native FP64 is 3."""
+    src = open(os.path.join(ROOT, "include", "bsechase.h")).read()
+    vals = {m.group(1): int(m.group(2))
+            for m in re.finditer(r"\b((?:BSE|CHASE)_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    for name, v in vals.items():
+        assert getattr(pkg, name) == v, name
+    assert vals["CHASE_MIXED_BF16X3"] == 2 and vals["CHASE_FP64_DFMA"] == 3
