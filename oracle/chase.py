@@ -28,6 +28,7 @@ states.
 import math
 
 import numpy as np
+import scipy.linalg
 
 from . import _lib
 from ._lib import Model, fortran, ptr
@@ -251,11 +252,11 @@ def chebyshev_filter(H, V, degrees, lower, c, e):
 
 
 def _trsm_right_upper(V, R):
-    """V R^{-1} for upper-triangular R, one column at a time."""
-    Q = np.empty_like(V)
-    for j in range(R.shape[0]):
-        Q[:, j] = (V[:, j] - Q[:, :j] @ R[:j, j]) / R[j, j]
-    return Q
+    """V R^{-1} for upper-triangular R: X R = V is R^T X^T = V^T, a triangular
+    solve (LAPACK trtrs through scipy, a library primitive)."""
+    X = scipy.linalg.solve_triangular(R, np.asarray(V).T, trans="T", lower=False,
+                                      check_finite=False)
+    return np.asfortranarray(X.T)
 
 
 def cholqr(V, shift=0.0):
