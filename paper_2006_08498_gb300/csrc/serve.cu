@@ -93,9 +93,18 @@ size_t estimate_run_bytes(int64_t N, int m, int nev, int precision) {
 }
 
 // Free least-recently-used resident eigenvectors until `need` more bytes fit.
-// Caller holds the lock.  Frees go on `st` after the data is no longer read
-// (nothing reads an unpinned resident block).
+// Nothing is freed when even evicting every unpinned block would not make
+// room (the request waits, and the warm-start data stays).  Caller holds the
+// lock.  Frees go on `st` after the data is no longer read (nothing reads an
+// unpinned resident block).
 void evict_for(BseServer *S, size_t need, cudaStream_t st) {
+    size_t evictable = 0;
+    for (uint64_t t : S->lru) {
+        auto r = S->reqs.find(t);
+        if (r != S->reqs.end() && r->second->d_evecs && r->second->pins == 0)
+            evictable += r->second->keep_bytes;
+    }
+    if (S->held - std::min(evictable, S->held) + need > S->budget) return;
     for (auto it = S->lru.begin(); it != S->lru.end() && S->held + need > S->budget;) {
         auto r = S->reqs.find(*it);
         if (r == S->reqs.end() || !r->second->d_evecs) {
@@ -268,14 +277,13 @@ int chase_server_submit(bsechase_ctx *ctx, const chase_request *req, uint64_t *t
     const int64_t N = bse_dim(req->Nk, req->Nv, req->Nc);
     const int m = req->nev + req->nex;
     if (N < 1 || req->nev < 1 || req->nex < 0 || m > N || m > 512 || !(req->tol > 0) ||
-        req->deg_max < 2 || req->degree_group < 0 ||
-        (req->precision != CHASE_FP64 && req->precision != CHASE_MIXED_FP32 &&
-         req->precision != CHASE_FP64_DFMA))
+        req->deg_max < 2 || req->degree_group < 0 || !precision_valid(req->precision))
         return fail(ctx, BSE_EINVAL, "invalid request%s");
     auto q = std::make_shared<Req>();
     q->rq = *req;
+    q->rq.precision = precision_mode(req->precision);
     q->N = N;
-    q->run_bytes = estimate_run_bytes(N, m, req->nev, req->precision);
+    q->run_bytes = estimate_run_bytes(N, m, req->nev, q->rq.precision);
     if (q->run_bytes > S->budget)
         return fail(ctx, BSE_ENOMEM, "request needs more than the whole HBM budget%s");
     q->t_submit = now_s();
