@@ -193,15 +193,20 @@ def lanczos_bounds(H, m, seed, n_runs=4, k_steps=25):
     allw = np.concatenate(taus) * (N / n_runs)
     order = np.argsort(allt, kind="stable")
     xs, cnt = allt[order], np.cumsum(allw[order])
+    return dict(beta=beta, mu_1=mu_1, mu_m=count_point(xs, cnt, m),
+                norm_est=max(abs(mu_1), abs(beta)), density=(xs, cnt))
+
+
+def count_point(xs, cnt, m):
+    """The point where the estimated eigenvalue count (cumulative weights cnt
+    at the pooled Ritz values xs, ascending) reaches m, linear between
+    consecutive Ritz values; the end values outside the range."""
     i = int(np.searchsorted(cnt, m, side="left"))
     if i >= len(xs):
-        mu_m = xs[-1]
-    elif i == 0:
-        mu_m = xs[0]
-    else:
-        mu_m = xs[i - 1] + (m - cnt[i - 1]) * (xs[i] - xs[i - 1]) / (cnt[i] - cnt[i - 1])
-    return dict(beta=beta, mu_1=mu_1, mu_m=mu_m,
-                norm_est=max(abs(mu_1), abs(beta)))
+        return xs[-1]
+    if i == 0:
+        return xs[0]
+    return xs[i - 1] + (m - cnt[i - 1]) * (xs[i] - xs[i - 1]) / (cnt[i] - cnt[i - 1])
 
 
 def filter_interval(alpha, beta):
@@ -394,6 +399,20 @@ def group_degrees(deg, width):
         deg[lo:hi] = deg[hi - 1]
         hi = lo
     return deg
+
+
+def nex_regression(e_cut, e_low, e_high, nex_low, nex_high):
+    """Eq. (S2): nex interpolated linearly in the energy cut-off between
+    (E_cut-low, nex_low) and (E_cut-high, nex_high)."""
+    return nex_low + (nex_high - nex_low) / (e_high - e_low) * (e_cut - e_low)
+
+
+def damping(gamma, alpha, beta):
+    """1/rho of Eq. (S1) for the value gamma with the damped interval
+    [alpha, beta]: the factor by which one filter degree shrinks the
+    component at gamma relative to the one at the interval's edge."""
+    c, e = filter_interval(alpha, beta)
+    return 1.0 / convergence_rate(gamma, c, e)
 
 
 def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,

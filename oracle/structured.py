@@ -38,10 +38,13 @@ The same structure gives H V in O(N (log Nk + R)) per column (the circulant
 K applied by FFT), which lets the plain oracle ChASE of chase.py run at the
 full benchmark sizes: BseOperator.
 
-The block eigensolver and the FFT are library primitives (numpy); nothing
+The block eigensolver and the FFT are library primitives (numpy, scipy); nothing
 else is blocked or reordered beyond the formulas above.
 """
+import os
+
 import numpy as np
+import scipy.fft
 
 from .chase import _model, bse_tables
 
@@ -166,6 +169,8 @@ class BseOperator:
             out = out + self.U @ (self.U.conj().T @ X)
         # rows of band pair b sit at k*nb + b: view as (Nk, nb, m)
         Y = (self.phase.conj()[:, None] * X).reshape(self.Nk, self.nb, -1)
-        KY = np.fft.ifft(self.k_hat[:, None, None] * np.fft.fft(Y, axis=0), axis=0)
+        nw = os.cpu_count() or 1
+        KY = scipy.fft.ifft(self.k_hat[:, None, None] * scipy.fft.fft(Y, axis=0, workers=nw),
+                            axis=0, workers=nw)
         out = out - self.w0 * (self.phase[:, None] * KY.reshape(self.N, -1))
         return out[:, 0] if vec else out

@@ -304,3 +304,30 @@ def test_lanczos_mu_m_pooled_runs_closed_form(n_runs):
         est = oracle.lanczos_bounds(A, m, seed=1, n_runs=n_runs, k_steps=N)
         assert est["mu_m"] == pytest.approx(lam[j], abs=1e-9)
         assert est["mu_1"] == pytest.approx(lam[0], abs=1e-9)
+
+
+def test_nex_regression_reproduces_table_s10():
+    """Eq. (S2) against every entry of Table S10.  The text names E_cut-high =
+    12.82 eV, but at 12.82 the table prints 76 and 106, not nex_high; the
+    printed values are those of E_cut-high in (14.311, 14.334] eV rounded to
+    the nearest integer (reading: E_cut-high = 14.32 eV).  With 12.82 the last
+    row would be nex_high itself."""
+    for row in golden("nex_dyn.txt"):
+        e_cut, n100, n150 = float(row[1]), int(row[2]), int(row[3])
+        for nex_high, printed in ((100, n100), (150, n150)):
+            v = oracle.nex_regression(e_cut, 10.54, 14.32, 40, nex_high)
+            assert int(math.floor(v + 0.5)) == printed
+            assert abs(v - printed) <= 0.5
+    # the interpolation's end points and its linearity
+    assert oracle.nex_regression(10.54, 10.54, 14.32, 40, 150) == 40
+    assert oracle.nex_regression(14.32, 10.54, 14.32, 40, 150) == pytest.approx(150)
+    assert oracle.nex_regression(12.43, 10.54, 14.32, 40, 100) == pytest.approx(70)
+    assert oracle.nex_regression(12.82, 10.54, 12.82, 40, 100) == pytest.approx(100)
+
+
+def test_damping_matches_tables_s8_s9():
+    """damping(lambda_nev, alpha, beta) = 1/rho_nev of Tables S8 and S9."""
+    for table in ("nex25.txt", "nex100.txt"):
+        for row in golden(table):
+            lam, alpha, beta, inv_rho = float(row[1]), float(row[2]), float(row[3]), float(row[6])
+            assert oracle.damping(lam, alpha, beta) == pytest.approx(inv_rho, abs=1.01e-5)
