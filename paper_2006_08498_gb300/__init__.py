@@ -24,6 +24,7 @@ CHASE_FP64, CHASE_MIXED_FP32, CHASE_MIXED_BF16X3, CHASE_FP64_DFMA = 0, 1, 2, 3
 # Every symbol include/bsechase.h declares.
 ABI_SYMBOLS = (
     "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
+    "bsechase_set_wait_limit",
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
     "chase_gram", "chase_gram_noalloc",
@@ -123,6 +124,8 @@ def load():
     L.bsechase_strerror.restype = ctypes.c_char_p
     L.bsechase_last_error.argtypes = [P]
     L.bsechase_last_error.restype = ctypes.c_char_p
+    L.bsechase_set_wait_limit.argtypes = [P, dbl]
+    L.bsechase_set_wait_limit.restype = i32
     L.bse_dim.argtypes = [i32, i32, i32]
     L.bse_dim.restype = i64
     L.bse_build_hamiltonian.argtypes = [P, u64, i32, i32, i32, ctypes.POINTER(Model), P, i64]
@@ -251,6 +254,10 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_wait_limit(self, seconds):
+        """Time limit of the bounded waits in the tensor-core kernels."""
+        self._check(load().bsechase_set_wait_limit(self._h, float(seconds)))
 
     def _check(self, rc, allow=(BSE_OK,)):
         if rc not in allow:

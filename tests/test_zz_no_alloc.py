@@ -46,6 +46,41 @@ def test_gram_noalloc_matches_gram_twice():
     assert np.all(np.abs(G2.cpu().numpy() - ref2) <= 1e-12 * (np.abs(Ah).T @ np.abs(C.cpu().numpy())))
 
 
+def test_gram_noalloc_self_product_and_side_stream():
+    """A^H A with the same pointer for both operands (the upper-tile path of
+    the Gram kernel and its mirrored reduction, the Cholesky QR use) at an
+    odd width, against chase_gram and numpy, twice; then one call on a side
+    stream."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_08498_gb300 import build
+    build.build()
+    K, m = 5001, 137
+    A = _dev(block(K, m, 31))
+    Ah = A.cpu().numpy()
+    ref_np = Ah.conj().T @ Ah
+    bound = np.abs(Ah).T @ np.abs(Ah)
+    with pkg.Context(0) as ctx:
+        ref = ctx.gram(A, A).cpu().numpy()
+    assert np.all(np.abs(ref - ref_np) <= 1e-12 * bound)
+    for call in range(2):
+        G = pkg.colmajor_empty(m, m, device=A.device)
+        G.fill_(float("nan"))
+        assert pkg.gram_noalloc(A, A, G) == pkg.BSE_OK
+        torch.cuda.synchronize()
+        got = G.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-12 * bound), "call %d" % call
+        assert np.all(np.abs(got - ref_np) <= 1e-12 * bound), "call %d" % call
+    side = torch.cuda.Stream(device=A.device)
+    side.wait_stream(torch.cuda.current_stream(A.device))
+    G = pkg.colmajor_empty(m, m, device=A.device)
+    with torch.cuda.stream(side):
+        G.fill_(float("nan"))
+        assert pkg.gram_noalloc(A, A, G, stream=side) == pkg.BSE_OK
+    side.synchronize()
+    assert np.all(np.abs(G.cpu().numpy() - ref) <= 1e-12 * bound)
+
+
 def test_gram_noalloc_rejects_oversize():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
