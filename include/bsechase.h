@@ -147,6 +147,15 @@ const char *bsechase_strerror(int status);
 /* Description of the last failure in `ctx` (empty string if none). */
 const char *bsechase_last_error(const bsechase_ctx *ctx);
 
+/* Time limit, in seconds (0 < seconds <= 60, default 2), of every bounded
+ * wait inside the context's tensor-core kernels (a wait for a copy, an MMA or
+ * a drained accumulator).  When a wait runs out, the kernel stops issuing
+ * work, waits for the copies and MMAs it already issued, releases its tensor
+ * memory and returns; the call then fails with BSE_ETIMEOUT and the context
+ * stays usable.  A short limit makes that path run on purpose (failure
+ * detection tests).  The paper has no counterpart.  Errors: BSE_EINVAL. */
+int bsechase_set_wait_limit(bsechase_ctx *ctx, double seconds);
+
 /* Dimension N = Nk * Nv * Nc of the BSE Hamiltonian (Sec. 2: the pair index
  * runs over valence bands, conduction bands and k-points); -1 if invalid. */
 int64_t bse_dim(int Nk, int Nv, int Nc);

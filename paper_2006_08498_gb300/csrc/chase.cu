@@ -198,6 +198,7 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     if ((rc = ensure(ctx, ctx->ozGE, (size_t)(Np + 512) * sizeof(int)))) return rc;
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
+    ctx->oh.wait_ns = ctx->wait_ns;
     CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
     return BSE_OK;
 }
@@ -353,6 +354,7 @@ OzGemmWork gen_work(bsechase_ctx *ctx) {
     w.f_len = (int64_t)(ctx->ozF.bytes / sizeof(int));
     w.P = (z_t *)ctx->ozP.p;
     w.p_bytes = ctx->ozP.bytes;
+    w.wait_ns = ctx->wait_ns;
     return w;
 }
 
@@ -688,6 +690,15 @@ const char *bsechase_strerror(int status) {
 }
 
 const char *bsechase_last_error(const bsechase_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int bsechase_set_wait_limit(bsechase_ctx *ctx, double seconds) {
+    if (!ctx) return BSE_EINVAL;
+    if (!(seconds > 0.0) || seconds > 60.0)
+        return fail(ctx, BSE_EINVAL, "wait limit must be in (0, 60] seconds%s");
+    ctx->wait_ns = (uint64_t)(seconds * 1e9);
+    if (ctx->wait_ns == 0) ctx->wait_ns = 1;
+    return BSE_OK;
+}
 
 int bsechase_create(bsechase_ctx **out, int device, void *stream) {
     if (!out) return BSE_EINVAL;

@@ -30,6 +30,7 @@ struct bsechase_ctx {
     DevBuf ozGA, ozGE;               // slices and exponents of op(A) for the general products
     bool gen_tc = false;             // N x m products of QR and Rayleigh-Ritz on the tensor cores
     int sms = 0;                     // multiprocessors of the device
+    uint64_t wait_ns = kDefaultWaitNs;  // bounded waits of the tensor-core kernel
     OzakiH oh;
     int64_t wsN = 0;
     int wsM = 0;

@@ -44,10 +44,16 @@ cudaError_t launch_zgemm_cn(int64_t m1, int64_t m2, int64_t K, const z_t *A, int
 // ---- FP64-accurate products on the BF16 tensor cores (ozaki.cu)
 // H sliced once per solve: A slices (ozaki_a_bytes), row exponents E
 // (padded length), and the TMA descriptor of the slices.
+// Time limit of each bounded mbarrier wait inside the tensor-core kernel
+// (nanoseconds of %globaltimer); on expiry the kernel winds down and reports
+// DEV_TIMEOUT.
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+
 struct OzakiH {
     int64_t N = 0, Np = 0;
     void *A = nullptr;
     int *E = nullptr;
+    uint64_t wait_ns = kDefaultWaitNs;
     alignas(64) unsigned char tmap[128];
 };
 int64_t ozaki_padded(int64_t N);
@@ -76,6 +82,7 @@ struct OzGemmWork {
     int64_t f_len = 0;
     z_t *P = nullptr;
     size_t p_bytes = 0;
+    uint64_t wait_ns = kDefaultWaitNs;
 };
 size_t ozaki_gen_a_bytes(int64_t M, int64_t K);
 size_t ozaki_gen_b_bytes(int64_t K, int n);

@@ -24,10 +24,10 @@
 // Keeping these accumulations to 64 terms matters: the tensor core's FP32
 // accumulator truncates toward zero, so a sum over the whole K would carry a
 // bias growing with K.  Diagonals 6 and 7 (weight <= 2^-32 of the leading
-// one) share one FP32 accumulator over the whole K: its truncation error is
-// at most one FP32 ulp of the running tail sum per K step of 16, i.e. below
-// (K/16) 2^-23 of the tail and about 2^-45 of the leading diagonal's scale
-// for K = 20000.  Diagonals > 7 are dropped.  The result is recombined in
+// one) share one FP32 accumulator over segments of kTailSeg K chunks; the
+// drain warps add the segments in FP32 registers (round to nearest).  Within
+// a segment the truncation error is at most one FP32 ulp of the running tail
+// sum per K step of 16.  Diagonals > 7 are dropped.  The result is recombined in
 // FP64, C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij), after the K splits' S and T
 // are summed (exactly, for S) by the reduction kernels.
 //
@@ -294,7 +294,12 @@ struct OzArgs {
     int csplit;       // K chunks per split
     int tx, ty, tz;   // work units: column tiles x row tiles x splits
     unsigned long long *P;   // raw partials of the splits, layout below
+    uint64_t wait_ns;        // limit of each bounded mbarrier wait
 };
+
+// Limit of each wait of the wind-down after an expired wait: long enough for
+// any copy or MMA already issued to finish.
+constexpr uint64_t kWindDownNs = 2000000000ull;
 
 // Raw partial product of split z for output (i, j): per (z, j) three blocks
 // of M 8-byte words, S of the real part (int64), S of the imaginary part
@@ -323,6 +328,18 @@ __host__ __device__ constexpr long long diag_bound(int g) {   // per chunk
     return 2 * kKC * b;
 }
 __host__ __device__ constexpr int drain_period(int g) { return g <= 3 ? 2 : 1; }
+// The tail (diagonals above kEx) accumulates in FP32 over at most
+// kTailSeg K chunks, then the drain warps add it into FP32 registers (round
+// to nearest) and the next segment starts from zero.  The tensor core's FP32
+// accumulation truncates, and over a whole K of 50000 the tail's error grew
+// to ~1e-11 of ||H|| ||y|| for eigenvector-like columns, enough to hold
+// converged residuals near 5e-11 and cost iterations at a tolerance of
+// 1e-10; over 2048 of K it stays several times smaller.
+constexpr int kTailSeg = 32;
+__host__ __device__ __forceinline__ bool tail_seg_start(int cl) { return cl % kTailSeg == 0; }
+__host__ __device__ __forceinline__ bool tail_seg_end(int cl, int nc) {
+    return (cl + 1) % kTailSeg == 0 || cl + 1 == nc;
+}
 static_assert(drain_period(2) * diag_bound(2) <= (1ll << 24) && drain_period(3) * diag_bound(3) <= (1ll << 24) &&
                   drain_period(4) * diag_bound(4) <= (1ll << 24) && drain_period(5) * diag_bound(5) <= (1ll << 24),
               "exact FP32 sums of the exact diagonals");
@@ -442,6 +459,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // read, accEmpty[1]: g = kEx too (the drain warps read them in the order
     // g = 2, ..., kEx)
     __shared__ uint64_t accFull[kNEx], accEmpty[2], tailFull, tailEmpty;
+    // mmaDone: the wind-down commit of the MMA thread (every MMA it issued
+    // has completed)
+    __shared__ uint64_t mmaDone;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -462,6 +482,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         tc::mbar_init(&accEmpty[1], kDrainWarps);
         tc::mbar_init(&tailFull, 1);
         tc::mbar_init(&tailEmpty, kDrainWarps);
+        tc::mbar_init(&mmaDone, 1);
         abort_flag = 0;
         tc::mbar_fence_init();
     }
@@ -485,6 +506,11 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         c1 = min(nch, c0 + args.csplit);
     };
 
+    // Arrivals the producer made on each full barrier: arrA[st] on fullA[st]
+    // (one per fill), arrB[g][par] on fullB[g][par] (S - 2 or 2 per phase).
+    // The wind-down after an expired wait completes a partly armed B phase
+    // and waits until every armed phase has landed (producer thread only).
+    int arrA[kAPairs] = {}, arrB[2][2] = {};
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
@@ -503,8 +529,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         if (order.kind[it] == 0) {
                             const int pp = order.idx[it];
                             const int ua = S * gc + pp, st = ua % kAPairs, n = ua / kAPairs;
-                            if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag)) { ok = false; break; }
+                            if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
                             tc::mbar_expect_tx(&fullA[st], 2 * kATile);
+                            arrA[st]++;
                             // parts (slice p, re) and (slice p, im) = 2 pp, 2 pp + 1 in the
                             // A tensor's part order
                             uint8_t *adst = sA + st * 2 * kATile;
@@ -513,12 +540,13 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         } else {
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
-                            if (n >= 1 && !tc::mbar_wait(q >= S - 2 ? &emptyBg : &emptyB[b], (n - 1) & 1, &abort_flag)) {
+                            if (n >= 1 && !tc::mbar_wait(q >= S - 2 ? &emptyBg : &emptyB[b], (n - 1) & 1, &abort_flag, args.wait_ns)) {
                                 ok = false;
                                 break;
                             }
                             uint64_t *fb = &fullB[q >= 3 ? 0 : 1][gc & 1];
                             tc::mbar_expect_tx(fb, kBSlice);
+                            arrB[q >= 3 ? 0 : 1][gc & 1]++;
                             uint8_t *bdst = sB + b * kBSlice;
                             // smem [-Yi | Yr | Yi] from parts 2, 0, 1
                             tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, fb);
@@ -539,20 +567,20 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const uint64_t adesc0 = tc::sdesc_sw128(sA), bdesc0 = tc::sdesc_sw128(sB);
             constexpr FirstPassOrder<S> kFirst;
             bool ok = true;
-            int gc = 0, uc = 0;
+            int gc = 0, uc = 0, ts = 0;   // ts: tail segments committed
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
                 int j0, z, c0, c1;
                 int64_t i0;
                 unit(u, j0, i0, z, c0, c1);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
-                    const bool first = (c == c0);
                     const int cl = c - c0, nc = c1 - c0;
+                    const bool seg0 = tail_seg_start(cl);
 #pragma unroll
                     for (int pi = 0; pi < S2; pi++) {
                         const int p = pi / 2 + 1, ri = pi & 1;
                         const int ua = S * gc + (p - 1), st = ua % kAPairs;
                         if (ri == 0) {
-                            if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag)) { ok = false; break; }
+                            if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
                             tc::fence_after();
                         }
                         const uint64_t a0 = adesc0 + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
@@ -565,16 +593,16 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 // B slices before the first MMA of their group (the
                                 // chunk's first MMA reads slice FirstPassOrder.q[0] >= 3)
                                 if ((q == kFirst.q[0] || q == 2) &&
-                                    !tc::mbar_wait(&fullB[q >= 3 ? 0 : 1][gc & 1], (gc >> 1) & 1, &abort_flag))
+                                    !tc::mbar_wait(&fullB[q >= 3 ? 0 : 1][gc & 1], (gc >> 1) & 1, &abort_flag, args.wait_ns))
                                     return false;
                                 // the previous chunk's accumulators g <= kEx - 1 before
                                 // the first of them (g = kEx - 1, q = 3), g = kEx at q = 4
                                 if ((g == kEx - 1 || g == kEx) && gc >= 1 &&
-                                    !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag))
+                                    !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag, args.wait_ns))
                                     return false;
-                                // the tail of the previous unit must have been read
-                                if (g > kEx && first && q == S && uc >= 1 &&
-                                    !tc::mbar_wait(&tailEmpty, (uc - 1) & 1, &abort_flag)) return false;
+                                // the tail of the previous segment must have been read
+                                if (g > kEx && seg0 && q == S && ts >= 1 &&
+                                    !tc::mbar_wait(&tailEmpty, (ts - 1) & 1, &abort_flag, args.wait_ns)) return false;
                                 tc::fence_after();
                             }
                             const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
@@ -582,9 +610,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             const uint64_t b0 =
                                 bdesc0 + (uint64_t)((b * kBSlice + (ri == 0 ? kBPart : 0)) >> 4);
                             // a fresh sum: every exact diagonal at its first pair
-                            // of the chunk, the tail at its first pair of the unit
+                            // of the chunk, the tail at its first pair of a segment
                             const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1 && cl % drain_period(g) == 0)
-                                                          : (first && pi == 0 && q == S);
+                                                          : (seg0 && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
                             const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
                             if (pi == 0 && coll == tc::A_FILL)
@@ -640,8 +668,12 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             if (p + 1 <= kEx && drain_due(p + 1, cl, nc)) tc::mma_commit(&accFull[p - 1]);
                         }
                     }
+                    // the chunk's last MMA is a tail pair (p = S, q = 1)
+                    if (ok && kTail && tail_seg_end(cl, nc)) {
+                        tc::mma_commit(&tailFull);
+                        ts++;
+                    }
                 }
-                if (ok && kTail) tc::mma_commit(&tailFull);
             }
         }
     } else {
@@ -652,20 +684,26 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         bool ok = true;
-        int gc = 0, uc = 0;
+        int gc = 0, ts = 0;                        // ts: tail segments read
         int dn[kNEx] = {};                         // drains of each exact diagonal so far
-        for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             int j0, z, c0, c1;
             int64_t i0;
             unit(u, j0, i0, z, c0, c1);
             long long Sx[kHalf];
 #pragma unroll
             for (int j = 0; j < kHalf; j++) Sx[j] = 0;
+            // the unit's outputs: row i, columns j0 + v < n; the FP32 tail of
+            // each is summed over the segments in its own slot of the raw
+            // partials (only this thread touches it; registers are full)
+            const int jn = args.n - j0;
+            const int64_t i = i0 + row;
+            float *Pt = (float *)args.P;
             for (int c = c0; c < c1 && ok; c++, gc++) {
 #pragma unroll 1
                 for (int g = 2; g <= kEx; g++) {
                     if (!drain_due(g, c - c0, c1 - c0)) continue;
-                    if (!tc::mbar_wait(&accFull[g - 2], dn[g - 2] & 1, &abort_flag)) { ok = false; break; }
+                    if (!tc::mbar_wait(&accFull[g - 2], dn[g - 2] & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
                     dn[g - 2]++;
                     tc::fence_after();
                     const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
@@ -687,37 +725,48 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     __syncwarp();
                     if (lane == 0 && g >= kEx - 1) tc::mbar_arrive(&accEmpty[g == kEx ? 1 : 0]);
                 }
-            }
-            uint32_t T[kHalf];           // FP32 bits of the tail
-#pragma unroll
-            for (int j = 0; j < kHalf; j++) T[j] = 0u;
-            if (ok && kTail) {
-                if (tc::mbar_wait(&tailFull, uc & 1, &abort_flag)) {
+                if (ok && kTail && tail_seg_end(c - c0, c1 - c0)) {
+                    if (!tc::mbar_wait(&tailFull, ts & 1, &abort_flag, args.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
                     tc::fence_after();
                     const uint32_t col = (uint32_t)(kNEx * kN + half * kHalf);
+                    // tail slot of column j0 + v: tb + v * (2 * kPartWords * M) floats
+                    float *tb = Pt + 2 * part_word(z, args.n, j0, 2, args.M, i) + half;
+                    const int64_t tstep = 2 * kPartWords * args.M;
+                    const bool seg_first = c - c0 < kTailSeg;   // the unit's first segment writes
+#pragma unroll 1
+                    for (int h = 0; h < kHalf; h += 8) {
+                        uint32_t r[8];
+                        tc::tmem_ld8(tmem + lane_addr + col + h, r);
+                        tc::tmem_wait_ld();
+                        if (i < args.M) {
 #pragma unroll
-                    for (int h = 0; h < kHalf; h += 16) tc::tmem_ld16(tmem + lane_addr + col + h, T + h);
-                    tc::tmem_wait_ld();
+                            for (int v = 0; v < 8; v++) {
+                                if (h + v >= jn) break;
+                                float *t = tb + (h + v) * tstep;
+                                const float x = __uint_as_float(r[v]);
+                                *t = seg_first ? x : *t + x;
+                            }
+                        }
+                    }
+                    ts++;
                     tc::fence_before();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&tailEmpty);
-                } else {
-                    ok = false;
                 }
             }
             if (!ok) break;
-            // Raw partials of this split: S (int64) and the FP32 tail T; the
+            // Raw partials of this split: S (int64) beside the FP32 tail; the
             // reduction kernels sum the splits exactly and recombine once.
-            const int jn = args.n - j0;                      // valid columns of the tile
-            const int64_t i = i0 + row;
             if (i < args.M) {
                 unsigned long long *P = args.P;
-                uint32_t *Pt = (uint32_t *)args.P;
 #pragma unroll
                 for (int v = 0; v < kHalf; v++) {
                     if (v >= jn) break;
                     P[part_word(z, args.n, j0 + v, half, args.M, i)] = (unsigned long long)Sx[v];
-                    Pt[2 * part_word(z, args.n, j0 + v, 2, args.M, i) + half] = T[v];
+                    if (!kTail) Pt[2 * part_word(z, args.n, j0 + v, 2, args.M, i) + half] = 0.f;
                 }
             }
         }
@@ -725,7 +774,40 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 
     tc::fence_before();
     __syncthreads();
-    if (abort_flag && threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.x);
+    if (abort_flag) {
+        // Wind-down after an expired wait: every role has left its loop, so
+        // no new copy or MMA is issued.  Before the shared memory and TMEM are
+        // released, the copies and MMAs already issued must finish:
+        //  - producer: a B phase armed by only some of its slices gets its
+        //    missing arrivals (the phase then completes once the bytes of
+        //    the armed slices land), then every armed phase of every full
+        //    barrier is waited for;
+        //  - MMA thread: one more commit, which arrives once every MMA it
+        //    issued has completed.
+        bool drained = true;
+        if (warp == 0 && lane == 0) {
+            constexpr int kArr[2] = {S - 2, 2};
+            for (int g = 0; g < 2; g++)
+                for (int par = 0; par < 2; par++) {
+                    while (arrB[g][par] % kArr[g] != 0) {
+                        tc::mbar_arrive(&fullB[g][par]);
+                        arrB[g][par]++;
+                    }
+                    const int ph = arrB[g][par] / kArr[g];
+                    if (ph > 0) drained &= tc::mbar_wait_for(&fullB[g][par], (ph - 1) & 1, kWindDownNs);
+                }
+            for (int st = 0; st < kAPairs; st++)
+                if (arrA[st] > 0) drained &= tc::mbar_wait_for(&fullA[st], (arrA[st] - 1) & 1, kWindDownNs);
+        }
+        if (warp == 1 && lane == 0) {
+            tc::mma_commit(&mmaDone);
+            drained &= tc::mbar_wait_for(&mmaDone, 0, kWindDownNs);
+        }
+        if (!drained) set_error(args.sc, DEV_TIMEOUT, -1 - (int)blockIdx.x);
+        tc::fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.x);
+    }
     if (warp == 1) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, kTmemCols);
@@ -941,6 +1023,7 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
     a.P = (unsigned long long *)partials;
+    a.wait_ns = oh.wait_ns;
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
@@ -1019,6 +1102,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     a.csplit = (a.nchunks + best - 1) / best;
     const int nsplit = (a.nchunks + a.csplit - 1) / a.csplit;
     a.P = (unsigned long long *)w.P;
+    a.wait_ns = w.wait_ns;
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;

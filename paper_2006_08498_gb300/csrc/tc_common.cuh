@@ -65,6 +65,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
     return true;
 }
 
+// Wait for phase `parity` of barrier b for at most limit_ns, without an
+// abort flag (the wind-down of a kernel whose normal waits have expired).
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *b, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try(b, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try(b, parity))
+        if (globaltimer() - t0 > limit_ns) return false;
+    return true;
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             uint64_t *bar) {
     asm volatile(
