@@ -3,11 +3,18 @@
 One step = the whole hot path on one synthetic BSE Hamiltonian: generate
 H on the device (Eq. (1) stand-in), then solve for the lowest nev
 eigenpairs (Lanczos, filter, QR, Rayleigh-Ritz, residuals/locking, output).
-Workload: N = 20000 (Nk = 1250, Nv = Nc = 4), nev = 100, nex = 40,
-deg_max = 36, tol = 1e-10, complex FP64.  The filter degrees of Eq. (S1) are
-raised in groups of 48 columns, the tile width of the tensor-core product
-(--degree-group; 0 keeps them unchanged).  H is 6.4 GB, far larger than L2,
-so no L2 flush is needed between steps.
+Workload: N = 50000 (Nk = 3125, Nv = Nc = 4; H is 40 GB), nev = 200,
+nex = 80, deg_max = 36, tol = 1e-10, complex FP64.  The filter degrees of
+Eq. (S1) are raised in groups of 48 columns, the tile width of the
+tensor-core product (--degree-group; 0 keeps them unchanged, and the line
+also reports one solve that way).  H is far larger than L2, so no L2 flush
+is needed between steps.
+
+After the timed steps the line adds: one end-to-end solve through the
+host-buffer entry point (H copied in, eigenvectors copied out); one solve
+in the mixed precision mode with its per-eigenpair differences from the
+FP64 solve; one solve with the degrees of Eq. (S1) unchanged; and the CPU
+oracle timed on the host's cores on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch under torch.distributed.run: every rank solves its own
@@ -25,9 +32,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="chase_N20000_nev100_nex40", Nk=1250, Nv=4, Nc=4, N=20000,
-                nev=100, nex=40, deg_max=36, tol=1e-10, seed=0, precision="fp64",
-                l2="inputs larger than L2 (H = 6.4 GB)", matvecs_per_solve=22540)
+WORKLOAD = dict(workload="chase_N50000_nev200_nex80", Nk=3125, Nv=4, Nc=4, N=50000,
+                nev=200, nex=80, deg_max=36, tol=1e-10, seed=0, precision="fp64",
+                l2="inputs larger than L2 (H = 40 GB)")
 METRIC = "chase_time_to_solution"
 UNIT = "s"
 
@@ -40,17 +47,11 @@ def _peaks():
         return {}
 
 
-# FP64 issue rate of the part: the measured DFMA peak when one is recorded
-# next to the bench (profiles/fp64_peak.txt, written from the DFMA-loop
-# probe), else the GB300 datasheet figure of 1.25 TFLOP/s.
-def _fp64_peak():
-    p = os.path.join(ROOT, "profiles", "fp64_peak.txt")
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        return float(d["fp64_tflops"]), "measured DFMA loop (profiles/fp64_peak.txt)"
-    except (OSError, KeyError, ValueError):
-        return 1.25, "datasheet (no measured FP64 peak recorded)"
+# FP64 issue rate of the part, measured on a GB300 with a loop of independent
+# DFMA chains over all SMs (1.005 TFLOP/s; DMMA tensor instructions 1.047):
+# the peak of the native-FP64 (DFMA) precision's roofline.
+FP64_PEAK_TFLOPS = 1.005
+FP64_PEAK_SOURCE = "measured DFMA-loop peak on a GB300 (1.005 TFLOP/s)"
 
 
 def _traffic(precision, workload_name):
@@ -167,11 +168,10 @@ def workload(args):
         W["N"] = args.nk * W["Nv"] * W["Nc"]
         W["workload"] = "chase_N%d_nev%d_nex%d" % (W["N"], args.nev, args.nex)
         W["l2"] = "H = %.2f GB" % (16e-9 * W["N"] ** 2)
-        W["matvecs_per_solve"] = 160 * (args.nev + args.nex)   # rough, for profiling runs
     return W
 
 
-PRECISIONS = {"fp64": 0, "mixed": 1, "fp64_dfma": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1, "fp64_dfma": 3}
 DTYPES = {"fp64": "f64 (H products: bf16 slices on tensor cores, exact int + f32 accumulation)",
           "mixed": "f64 with f32-level filter sweeps (4 bf16 slices, exact accumulation)",
           "fp64_dfma": "f64"}
@@ -189,7 +189,7 @@ def roofline(precision, st, N, workload_name):
     fp64_eq = st["filter_tflops"]
     tr = _traffic(precision, workload_name)
     if precision == "fp64_dfma":
-        peak, src = _fp64_peak()
+        peak, src = FP64_PEAK_TFLOPS, FP64_PEAK_SOURCE
         return {"kernel": "zgemm_nn_kernel (filter H*Y, Chebyshev epilogue, DFMA)",
                 "bound": "alu", "achieved": fp64_eq, "peak": peak, "unit": "TFLOP/s",
                 "frac": fp64_eq / peak, "peak_source": src,
@@ -211,52 +211,136 @@ def roofline(precision, st, N, workload_name):
             "fp64_equivalent_filter_tflops": fp64_eq}
 
 
-def cpu_baseline_sample(W, seconds_budget=25.0):
-    """The oracle, as it stands, on the host cores: builds the workload's H
-    and times single filter matrix products over the full search space
-    (m = 140 columns), then projects one solve from the per-matvec time and
-    the matvec count of the device solve.  Returns (seconds per solve,
-    sample description, cores)."""
+def cpu_oracle_sample(W, n_cols=48):
+    """The CPU oracle, as it stands, on every host core, on the workload's own
+    matrix: builds H (oracle.build_h), then times one filter product over
+    n_cols columns (oracle.chebyshev_filter with degree 1), the QR phase on
+    the full N x m search space (oracle.qr) and the Rayleigh-Ritz steps other
+    than its product with H (projection, oracle.eigh of the m x m matrix,
+    back-transforms, residual norms).  Returns the timings in seconds."""
     import numpy as np
     import oracle
+    N, m = W["N"], W["nev"] + W["nex"]
     t0 = time.perf_counter()
     H = oracle.build_h(W["seed"], W["Nk"], W["Nv"], W["Nc"])
     t_build = time.perf_counter() - t0
-    m = W["nev"] + W["nex"]
-    V = oracle.random_block(0, oracle.STREAM_START, W["N"], m)
-    c, e, lower = 8.0, 5.0, 0.8
-    reps, t_mv = 0, 0.0
-    while reps < 1 or (t_mv + t_build < seconds_budget and reps < 8):
-        t0 = time.perf_counter()
-        oracle.chebyshev_filter(H, V, np.full(m, 1), lower, c, e)
-        t_mv += time.perf_counter() - t0
-        reps += 1
-    per_matvec = t_mv / (reps * m)
-    return per_matvec, t_build, reps, os.cpu_count()
+    V = oracle.random_block(W["seed"], oracle.STREAM_START, N, m)
+    nc = min(n_cols, m)
+    t0 = time.perf_counter()
+    oracle.chebyshev_filter(H, V[:, :nc], np.ones(nc, dtype=np.int64), 0.8, 8.0, 5.0)
+    t_mv = (time.perf_counter() - t0) / nc
+    del H
+    t_qr, t_rr = _oracle_qr_rr(V)
+    return dict(t_build=t_build, t_mv=t_mv, t_qr=t_qr, t_rr=t_rr, n_cols=nc)
+
+
+def _oracle_qr_rr(V):
+    """Seconds of one oracle QR phase on V and of one Rayleigh-Ritz without
+    its H product (W = H Q stood in by a block of the same shape)."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    Q = oracle.qr(None, V)
+    t_qr = time.perf_counter() - t0
+    W_ = V
+    t0 = time.perf_counter()
+    G = Q.conj().T @ W_
+    G = (G + G.conj().T) / 2.0
+    theta, Y = oracle.eigh(G)
+    Vr, HVr = Q @ Y, W_ @ Y
+    oracle.residuals(HVr, Vr, theta, 1.0)
+    t_rr = time.perf_counter() - t0
+    return t_qr, t_rr
+
+
+def cpu_oracle_single_thread(W, Nk_small=313, n_cols=48):
+    """The same sample with one thread (a child process with the BLAS and
+    OpenMP thread counts at 1), on the generator's matrix at Nk_small
+    k-points (N_s = 16 Nk_small), scaled to the workload's N: products by
+    (N/N_s)^2, QR and Rayleigh-Ritz by N/N_s.  None if the child fails."""
+    code = (
+        "import sys, json; sys.path.insert(0, %r)\n"
+        "import bench\n"
+        "W = dict(bench.WORKLOAD, Nk=%d); W['N'] = 16 * W['Nk']\n"
+        "print(json.dumps(bench.cpu_oracle_sample(W, %d)))\n" % (ROOT, Nk_small, n_cols))
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                           text=True, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        return None
+    f = W["N"] / (16.0 * Nk_small)
+    return dict(t_build=d["t_build"] * f * f, t_mv=d["t_mv"] * f * f,
+                t_qr=d["t_qr"] * f, t_rr=d["t_rr"] * f, n_small=16 * Nk_small)
+
+
+def project_solve(sample, counts):
+    """Seconds of one oracle solve: build, every H*vector product at the
+    sampled per-column time, and per iteration one QR and one Rayleigh-Ritz."""
+    return (sample["t_build"] + sample["t_mv"] * counts["matvecs"] +
+            counts["iters"] * (sample["t_qr"] + sample["t_rr"]))
+
+
+def oracle_counts(W, degree_group):
+    """Iterations and H*vector products of the oracle's own ChASE on this
+    workload: the plain oracle ChASE run to convergence with its products
+    through the structured operator of the synthetic Hamiltonian (exact
+    H V in O(N log N) per column), timed."""
+    import oracle
+    t0 = time.perf_counter()
+    op = oracle.structured.BseOperator(W["seed"], W["Nk"], W["Nv"], W["Nc"])
+    r = oracle.chase(op, W["nev"], W["nex"], tol=W["tol"], deg_max=W["deg_max"],
+                     degree_group=degree_group)
+    return dict(iters=r["iters"], matvecs=r["matvecs"], status=r["status"],
+                seconds=time.perf_counter() - t0)
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle on the host cores, on a bounded sample
-    of the same workload, projected to one solve."""
+    """Reference arm: the CPU oracle on the host cores.  Once (before the
+    steps): the oracle's own ChASE on this workload through the structured
+    operator, for its iteration and product counts.  Each step: the oracle
+    timed on a bounded sample of the workload's dense matrix (one filter
+    product over 16 columns, one QR phase, one Rayleigh-Ritz without its H
+    product), projected to one dense-matrix solve with those counts."""
     if rank != 0:
         return
+    import numpy as np
+    import oracle
     W = workload(args)
-    per_mv, t_build, reps, cores = cpu_baseline_sample(W)
-    # H*vector products of one solve of this workload: the oracle and the
-    # device path take the same iterations and degrees (checked by the parity
-    # tests), so the count of the device's FP64 solve stands for the oracle's.
-    mv_total = float(W["matvecs_per_solve"])
-    t_solve = t_build + per_mv * mv_total
-    sample = ("oracle build_h at N=%d (%.1f s) + %d filter product(s) over %d columns; "
-              "solve projected as build + %d matvecs x %.3e s"
-              % (W["N"], t_build, reps, W["nev"] + W["nex"], mv_total, per_mv))
+    counts = oracle_counts(W, args.degree_group)
+    N, m = W["N"], W["nev"] + W["nex"]
+    t0 = time.perf_counter()
+    H = oracle.build_h(W["seed"], W["Nk"], W["Nv"], W["Nc"])
+    t_build = time.perf_counter() - t0
+    V = oracle.random_block(W["seed"], oracle.STREAM_START, N, m)
+    nc = 16
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.chebyshev_filter(H, V[:, step % (m - nc):step % (m - nc) + nc],
+                                np.ones(nc, dtype=np.int64), 0.8, 8.0, 5.0)
+        t_mv = (time.perf_counter() - t0) / nc
+        t_qr, t_rr = _oracle_qr_rr(V)
+        if step >= args.warmup:
+            vals.append(project_solve(dict(t_build=t_build, t_mv=t_mv, t_qr=t_qr, t_rr=t_rr),
+                                      counts))
+    t_solve = float(np.mean(vals))
+    sample = ("per step: oracle filter product over %d of %d columns of the dense N=%d matrix, "
+              "one QR phase and one Rayleigh-Ritz (without its H product), projected to one "
+              "solve with the oracle's own counts (%d iterations, %d H*v products; its ChASE "
+              "through the structured operator took %.1f s) plus build_h (%.1f s)"
+              % (nc, m, N, counts["iters"], counts["matvecs"], counts["seconds"], t_build))
     line = {"impl": "reference", "metric": METRIC, "value": t_solve, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_solve * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": W,
-            "cpu_baseline": {"value": t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "config": dict(W, precision=args.precision, degree_group=args.degree_group,
+                           parallelism="single"),
+            "projected": True,
+            "oracle_counts": counts,
+            "cpu_baseline": {"value": t_solve, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": t_solve, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -301,9 +385,11 @@ def run_ours(args, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    stats = []
+    stats, stats_evals = [], []
     for _ in range(args.steps):
-        stats.append(step()[3])
+        out = step()
+        stats.append(out[3])
+        stats_evals.append(out[0])
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -326,6 +412,44 @@ def run_ours(args, rank, world, local_rank):
             ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh,
                            precision=prec, degree_group=args.degree_group)
         e2e_s = slowest((time.perf_counter() - t0) / e2e_steps, dist, device="cuda")
+        del Hh, Hcol, Zh
+
+    # one solve each of the other modes on the same matrix, after the timed
+    # region: the mixed precision mode (per-eigenpair differences from the
+    # FP64 solve of the last timed step) and the degrees of Eq. (S1) as they
+    # are (no degree groups)
+    extras = {}
+    if not args.no_extras and world == 1 and args.precision == "fp64":
+        ev_ref = stats_evals[-1]
+        V_ref = evecs.clone()
+
+        def timed(**kw):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return out, e0.elapsed_time(e1) / 1e3
+
+        (ev_m, V_m, r_m, st_m), t_m = timed(precision=PRECISIONS["mixed"],
+                                             degree_group=args.degree_group)
+        rel = np.abs(ev_m - ev_ref) / np.abs(ev_ref)
+        # per pair: 1 - |<v_mixed, v_fp64>| (phase-free overlap of the unit vectors)
+        ov = torch.abs(torch.sum(V_m.conj() * V_ref, dim=0)).cpu().numpy()
+        extras["mixed"] = {
+            "value": t_m, "unit": UNIT, "iters": st_m["iters"],
+            "filter_matvecs": st_m["filter_matvecs"],
+            "filter_matvecs_low": st_m["filter_matvecs_low"],
+            "max_resid": float(np.max(r_m)),
+            "eval_rel_diff_vs_fp64": {"max": float(np.max(rel)), "median": float(np.median(rel)),
+                                      "per_pair": [float("%.3g" % x) for x in rel]},
+            "evec_one_minus_overlap_vs_fp64": {"max": float(np.max(1.0 - ov)),
+                                               "median": float(np.median(1.0 - ov))}}
+        del V_m
+        (ev_0, V_0, r_0, st_0), t_0 = timed(precision=prec, degree_group=0)
+        extras["degree_group_0"] = {"value": t_0, "unit": UNIT, "iters": st_0["iters"],
+                                    "matvecs": st_0["matvecs"], "max_resid": float(np.max(r_0))}
+        del V_0, V_ref
 
     if rank == 0:
         st = stats[-1]
@@ -351,14 +475,26 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats) + 2 * args.steps),
             "clocks": ck,
         }
+        line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
-            per_mv, t_build, reps, cores = cpu_baseline_sample(W)
-            t_cpu = t_build + per_mv * st["matvecs"]
+            counts = dict(iters=st["iters"], matvecs=st["matvecs"])
+            smp = cpu_oracle_sample(W)
+            t_cpu = project_solve(smp, counts)
+            one = cpu_oracle_single_thread(W)
             line["cpu_baseline"] = {
-                "value": t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": ("oracle build_h at N=%d (%.1f s) + %d filter product(s) over %d "
-                           "columns (%.3e s/matvec), projected to this solve's %d matvecs"
-                           % (N, t_build, reps, nev + nex, per_mv, st["matvecs"]))}
+                "value": t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "projected": True,
+                "sample": ("oracle on the dense N=%d matrix, all cores: build_h %.1f s, filter "
+                           "product over %d columns %.3e s per column, QR phase %.2f s, "
+                           "Rayleigh-Ritz without its H product %.2f s; projected with this "
+                           "solve's %d iterations and %d H*v products"
+                           % (N, smp["t_build"], smp["n_cols"], smp["t_mv"], smp["t_qr"],
+                              smp["t_rr"], counts["iters"], counts["matvecs"])),
+                "single_thread": None if one is None else {
+                    "value": project_solve(one, counts), "unit": UNIT, "cores": 1,
+                    "projected": True,
+                    "sample": ("the same oracle steps with one thread at N=%d, products "
+                               "scaled by N^2, QR and Rayleigh-Ritz by N" % one["n_small"])}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -452,6 +588,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed-precision and Eq. (S1)-degree solves after the timed steps")
     ap.add_argument("--clock-log", default=None,
                     help="keep the nvidia-smi samples of the timed region in this CSV ({rank} = rank)")
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
