@@ -114,6 +114,17 @@ typedef struct {
                             (48 columns), so 48 filters some columns further
                             at no cost; never lowers a degree.  No counterpart
                             in the paper. */
+    double nex_damping;  /* 0 (default): nex fixed.  > 0: the nex tuner (the
+                            Supplement's nex study, Tables S8/S9: the damping
+                            1/rho_nev of Eq. (S1) with gamma = lambda_nev sets
+                            the convergence rate, and a larger nex lowers it).
+                            After each Rayleigh-Ritz from the second on, the
+                            damping is evaluated with gamma = the nev-th Ritz
+                            value and alpha = the largest; once two consecutive
+                            values differ by at most 0.02 and the value exceeds
+                            nex_damping, nex grows once to min(max(2 nex,
+                            nex + 8), min(N, 512) - nev).  The new columns are
+                            the seeded start block's next columns. */
 } chase_opts;
 
 /* Per-solve statistics (times in milliseconds, CUDA events on the stream). */
@@ -135,6 +146,8 @@ typedef struct {
     int64_t tc_kernel_launches; /* launches timed                             */
     double tc_kernel_tflops;    /* executed BF16 tensor flops (8 per complex  */
                                 /* multiply-add per slice pair) / duration    */
+    int nex_used;               /* nex at the end (differs from the argument
+                                   when the nex tuner grew it)                */
 } chase_stats;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
@@ -278,6 +291,7 @@ typedef struct {
     uint64_t warm_ticket;    /* 0, or a ticket whose eigenvectors (same N) start
                                 this solve if that request has finished       */
     int degree_group;        /* as chase_opts.degree_group (0: Eq. (S1))       */
+    double nex_damping;      /* as chase_opts.nex_damping (0: nex fixed)       */
 } chase_request;
 
 typedef struct {

@@ -20,6 +20,6 @@ from . import structured  # noqa: F401
 from .chase import (  # noqa: F401
     STREAM_EXCHANGE, STREAM_LANCZOS, STREAM_START, STREAM_THETA, STREAM_XI,
     bse_elements, bse_tables, build_h, chase, chebyshev_filter, cholesky, cholqr,
-    convergence_rate, damping, default_model, degree_cap, degrees, eigh, filter_interval, group_degrees, count_point,
+    convergence_rate, damping, default_model, degree_cap, degrees, eigh, filter_interval, group_degrees, grown_nex, count_point,
     lanczos_bounds, lock_count, nex_regression, normalize_phase, qr, random_block,
     rayleigh_ritz, residuals, splitmix64, tridiag_eig, uniform)

@@ -415,9 +415,18 @@ def damping(gamma, alpha, beta):
     return 1.0 / convergence_rate(gamma, c, e)
 
 
+def grown_nex(nex, nev, N, m_max=512):
+    """The larger nex of the nex tuner: doubled (and at least 8 more), within
+    the search-space limit nev + nex <= min(N, m_max)."""
+    return min(max(2 * nex, nex + 8), min(N, m_max) - nev)
+
+
+NEX_SETTLED = 0.02
+
+
 def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
           seed=0, V0=None, lanczos_runs=4, lanczos_steps=25, trace=False,
-          degree_group=0):
+          degree_group=0, nex_damping=0.0):
     """Lowest nev eigenpairs of the Hermitian H by ChASE.
 
     Lanczos estimate, then per iteration: interval (c, e) from (alpha,
@@ -426,6 +435,15 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
     smallest Ritz value); new degrees; unlocked columns sorted by degree.
     degree_group > 0 raises the degrees in groups (group_degrees) before
     each filter; 0 keeps the degrees of Eq. (S1).
+    nex_damping > 0 turns on the nex tuner (reading of the Supplement's nex
+    study: the damping 1/rho_nev of the last wanted pair, Eq. (S1) with
+    gamma = lambda_nev, sets the convergence rate, and a larger nex lowers
+    it).  After each Rayleigh-Ritz from the second on, the damping is
+    evaluated with gamma = the nev-th Ritz value and alpha = the largest;
+    once two consecutive values differ by at most NEX_SETTLED (the first
+    iterations' Ritz values above lambda_nev are still far off) and the value
+    exceeds nex_damping, nex grows once to grown_nex.  The new columns are the
+    seeded start block's next columns, filtered with deg_max.
     Returns a dict with ascending eigenvalues, eigenvectors (phase-
     normalised), residuals, iteration and matvec counts, and a status
     ("ok" or "noconv")."""
@@ -449,6 +467,7 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
     history = []
     it = 0
     status = "noconv"
+    damp_prev, grown = None, False
     while it < max_iter:
         it += 1
         c, e = filter_interval(alpha, beta)
@@ -458,6 +477,7 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
         deg = group_degrees(deg, degree_group)
         Vf, mv = chebyshev_filter(H, V[:, locked:], deg, lower, c, e)
         matvecs += mv
+        locked0 = locked
         Q = qr(V[:, :locked], Vf)
         theta, Vr, HVr = rayleigh_ritz(H, Q)
         matvecs += Q.shape[1]
@@ -484,6 +504,20 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
         lam[locked:] = th_u[perm]
         res[locked:] = r_u[perm]
         deg = d[perm]
+        if nex_damping > 0.0 and not grown and nev - 1 - locked0 >= 0:
+            dmp = damping(theta[nev - 1 - locked0], alpha, beta)
+            if (damp_prev is not None and abs(dmp - damp_prev) <= NEX_SETTLED
+                    and dmp > nex_damping):
+                grown = True
+                nex2 = grown_nex(nex, nev, N)
+                if nex2 > nex:
+                    m2 = nev + nex2
+                    V = np.concatenate([V, random_block(seed, STREAM_START, N, m2)[:, m:]], axis=1)
+                    lam = np.concatenate([lam, np.full(m2 - m, alpha)])
+                    res = np.concatenate([res, np.full(m2 - m, np.inf)])
+                    deg = np.concatenate([deg, np.full(m2 - m, deg_max, dtype=np.int64)])
+                    nex, m = nex2, m2
+            damp_prev = dmp
     k = nev
     res_out = res[:k].copy()
     res_out[locked:] = np.inf          # not converged: reported as +inf
@@ -492,4 +526,5 @@ def chase(H, nev, nex, tol=1e-10, deg_max=36, deg_init=20, max_iter=50,
     evecs = normalize_phase(V[:, :k][:, order])
     resid = res_out[order]
     return dict(evals=evals, evecs=evecs, resid=resid, iters=it,
-                matvecs=matvecs, status=status, lanczos=est, history=history)
+                matvecs=matvecs, status=status, lanczos=est, history=history,
+                nex=nex)

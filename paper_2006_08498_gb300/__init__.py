@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
                 ("lanczos_steps", ctypes.c_int), ("lanczos_vecs", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("d_V0", ctypes.c_void_p),
                 ("ldv0", ctypes.c_int64), ("n_v0", ctypes.c_int),
-                ("degree_group", ctypes.c_int)]
+                ("degree_group", ctypes.c_int), ("nex_damping", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
                 ("lower", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64),
                 ("tc_kernel_ms", ctypes.c_double), ("tc_kernel_launches", ctypes.c_int64),
-                ("tc_kernel_tflops", ctypes.c_double)]
+                ("tc_kernel_tflops", ctypes.c_double), ("nex_used", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,7 +75,8 @@ class Request(ctypes.Structure):
                 ("Nc", ctypes.c_int), ("use_model", ctypes.c_int), ("model", Model),
                 ("nev", ctypes.c_int), ("nex", ctypes.c_int), ("tol", ctypes.c_double),
                 ("deg_max", ctypes.c_int), ("precision", ctypes.c_int),
-                ("warm_ticket", ctypes.c_uint64), ("degree_group", ctypes.c_int)]
+                ("warm_ticket", ctypes.c_uint64), ("degree_group", ctypes.c_int),
+                ("nex_damping", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -285,8 +286,10 @@ class Context:
 
     # -------------------------------------------------------------- solve
     @staticmethod
-    def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group=0):
-        o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0, degree_group)
+    def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group=0,
+              nex_damping=0.0):
+        o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0, degree_group,
+                 nex_damping)
         if V0 is not None:
             o.d_V0 = ctypes.c_void_p(V0.data_ptr())
             o.ldv0 = _ld(V0)
@@ -295,7 +298,7 @@ class Context:
 
     def solve(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64, deg_init=20,
               max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0, V0=None,
-              evecs=None, allow_noconv=False, degree_group=0):
+              evecs=None, allow_noconv=False, degree_group=0, nex_damping=0.0):
         """Lowest nev eigenpairs of the device Hermitian H (column-major).
         Returns (evals ndarray, evecs tensor N x nev, resid ndarray, stats)."""
         N = H.shape[0]
@@ -304,7 +307,8 @@ class Context:
         if evecs is None:
             evecs = colmajor_empty(N, nev, device=H.device)
         st = Stats()
-        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group)
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group,
+                       nex_damping)
         rc = load().chase_solve(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), nev, nex,
                                 tol, deg_max, precision, ctypes.byref(o), _dp(evals),
                                 ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
@@ -393,7 +397,7 @@ class Context:
         self._check(load().chase_server_destroy(self._h))
 
     def submit(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
-               model=None, warm_ticket=0, degree_group=0):
+               model=None, warm_ticket=0, degree_group=0, nex_damping=0.0):
         """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc);
         returns its ticket."""
         md = dict(DEFAULT_MODEL)
@@ -402,7 +406,7 @@ class Context:
         r = Request(seed, Nk, Nv, Nc, 1 if model else 0,
                     Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
                           int(md["rank_x"])),
-                    nev, nex, tol, deg_max, precision, warm_ticket, degree_group)
+                    nev, nex, tol, deg_max, precision, warm_ticket, degree_group, nex_damping)
         t = ctypes.c_uint64(0)
         self._check(load().chase_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value

@@ -473,11 +473,32 @@ int validate_solve(bsechase_ctx *ctx, const void *H, int64_t N, int64_t ldh, int
 
 }  // namespace
 
+namespace {
+
+// 1/rho of Eq. (S1) for gamma with the damped interval [alpha, beta]
+double damping_of(double gamma, double alpha, double beta) {
+    const double c = (alpha + beta) / 2.0, e = (beta - alpha) / 2.0;
+    const double t = (gamma - c) / e;
+    if (fabs(t) <= 1.0) return 1.0;
+    return 1.0 / (fabs(t) + sqrt(t * t - 1.0));
+}
+
+// the larger nex of the nex tuner: doubled (at least 8 more), nev + nex <=
+// min(N, 512)
+int grown_nex(int nex, int nev, int64_t N) {
+    const int top = (int)std::min<int64_t>(N, kMaxM) - nev;
+    return std::min(std::max(2 * nex, nex + 8), top);
+}
+
+constexpr double kNexSettled = 0.02;   // consecutive dampings this close: settled
+
+}  // namespace
+
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
                  z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats) {
     int rc;
-    const int m = nev + nex;
+    int m = nev + nex;
     chase_opts o{};
     o.deg_init = 20;
     o.max_iter = 50;
@@ -494,10 +515,16 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         o.ldv0 = opts->ldv0;
         o.n_v0 = opts->n_v0;
         o.degree_group = opts->degree_group;
+        o.nex_damping = opts->nex_damping;
     }
     if (o.d_V0 && (o.n_v0 < 0 || o.ldv0 < N)) return fail(ctx, BSE_EINVAL, "bad warm-start block%s");
     if (o.degree_group < 0) return fail(ctx, BSE_EINVAL, "degree_group must be >= 0%s");
-    if ((rc = ensure_workspace(ctx, N, m))) return rc;
+    if (!(o.nex_damping >= 0.0 && o.nex_damping < 1.0))
+        return fail(ctx, BSE_EINVAL, "nex_damping must be in [0, 1)%s");
+    const bool tuner = o.nex_damping > 0.0;
+    // the workspace holds the largest search space the tuner may grow to
+    const int m_cap = tuner ? nev + std::max(nex, grown_nex(nex, nev, N)) : m;
+    if ((rc = ensure_workspace(ctx, N, m_cap))) return rc;
     Small s = small_layout(ctx, m);
     z_t *V = (z_t *)ctx->V.p, *B2 = (z_t *)ctx->B2.p, *B3 = (z_t *)ctx->B3.p;
     Timer tm{ctx};
@@ -509,7 +536,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     tm.mark(0);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     Hop op{H, N, ldh, precision_uses_tc(precision)};
-    if ((rc = hop_prepare(ctx, op, m))) return rc;
+    if ((rc = hop_prepare(ctx, op, m_cap))) return rc;
     GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
     tm.mark(1);
@@ -530,9 +557,12 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     std::vector<int> perm(m);
     int locked = 0, it = 0;
     bool converged = false;
+    double damp_prev = -1.0;
+    bool grown = false;
     while (it < o.max_iter) {
         it++;
         const int ma = m - locked;
+        const int locked0 = locked;
         const double c = (alpha + beta) / 2.0, e = (beta - alpha) / 2.0;
         z_t *Va = V + (int64_t)locked * N;
         // cap the degrees so the filtered block stays numerically full rank:
@@ -601,6 +631,29 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
             converged = true;
             break;
         }
+        // nex tuner: the damping of the nev-th Ritz value (th holds the Ritz
+        // values of the unlocked block in ascending order)
+        if (tuner && !grown && nev - 1 - locked0 >= 0) {
+            const double d = damping_of(th[nev - 1 - locked0], alpha, beta);
+            if (damp_prev >= 0.0 && fabs(d - damp_prev) <= kNexSettled && d > o.nex_damping) {
+                grown = true;
+                const int nex2 = grown_nex(nex, nev, N);
+                if (nex2 > nex) {
+                    const int m2 = nev + nex2;
+                    CK(launch_random_block(o.seed, 5, N, m2 - m, m, V, N, ctx->st));
+                    hdeg.resize(m2, deg_max);
+                    for (int j = m - locked; j < m2 - locked; j++) hdeg[j] = deg_max;
+                    lam.resize(m2, alpha);
+                    res.resize(m2, INFINITY);
+                    th.resize(m2);
+                    rr.resize(m2);
+                    perm.resize(m2);
+                    nex = nex2;
+                    m = m2;
+                }
+            }
+            damp_prev = d;
+        }
     }
     // output: locked pairs sorted ascending
     tm.mark(2);
@@ -651,6 +704,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         stats->tc_kernel_ms = ctx->k_ms;
         stats->tc_kernel_launches = ctx->k_launches;
         stats->tc_kernel_tflops = ctx->k_ms > 0 ? ctx->k_flops / (ctx->k_ms * 1e9) : 0.0;
+        stats->nex_used = nex;
     }
     if (!converged) return fail(ctx, BSE_ENOCONV, "not converged after max_iter iterations%s");
     return BSE_OK;

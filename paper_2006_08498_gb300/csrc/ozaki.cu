@@ -24,10 +24,10 @@
 // Keeping these accumulations to 64 terms matters: the tensor core's FP32
 // accumulator truncates toward zero, so a sum over the whole K would carry a
 // bias growing with K.  Diagonals 6 and 7 (weight <= 2^-32 of the leading
-// one) share one FP32 accumulator over segments of kTailSeg K chunks; the
-// drain warps add the segments in FP32 registers (round to nearest).  Within
-// a segment the truncation error is at most one FP32 ulp of the running tail
-// sum per K step of 16.  Diagonals > 7 are dropped.  The result is recombined in
+// one) share one FP32 accumulator over the K chunks of one work unit (at most
+// kUnitChunks), whose sums over K splits are added in FP32 by the reduction:
+// within a unit the truncation error is at most one FP32 ulp of the running
+// tail sum per K step of 16.  Diagonals > 7 are dropped.  The result is recombined in
 // FP64, C_ij = 2^(E_i + F_j) (S_ij 2^-40 + T_ij), after the K splits' S and T
 // are summed (exactly, for S) by the reduction kernels.
 //
@@ -328,18 +328,16 @@ __host__ __device__ constexpr long long diag_bound(int g) {   // per chunk
     return 2 * kKC * b;
 }
 __host__ __device__ constexpr int drain_period(int g) { return g <= 3 ? 2 : 1; }
-// The tail (diagonals above kEx) accumulates in FP32 over at most
-// kTailSeg K chunks, then the drain warps add it into FP32 registers (round
-// to nearest) and the next segment starts from zero.  The tensor core's FP32
-// accumulation truncates, and over a whole K of 50000 the tail's error grew
-// to ~1e-11 of ||H|| ||y|| for eigenvector-like columns, enough to hold
-// converged residuals near 5e-11 and cost iterations at a tolerance of
-// 1e-10; over 2048 of K it stays several times smaller.
-constexpr int kTailSeg = 32;
-__host__ __device__ __forceinline__ bool tail_seg_start(int cl) { return cl % kTailSeg == 0; }
-__host__ __device__ __forceinline__ bool tail_seg_end(int cl, int nc) {
-    return (cl + 1) % kTailSeg == 0 || cl + 1 == nc;
-}
+// The tail (diagonals above kEx) accumulates in FP32 over one work unit,
+// and a unit spans at most kUnitChunks K chunks (the host splits K so).
+// The tensor core's FP32 accumulation truncates: over a whole K of 50000 the
+// tail's error grew to ~1e-11 of ||H|| ||y|| for eigenvector-like columns,
+// enough to hold converged residuals near 5e-11 and cost 7 of 15 iterations
+// at a tolerance of 1e-10 (N = 50000); over 2048 of K it is about 5e-12 and
+// the solve takes the oracle's 8 iterations.
+constexpr int kUnitChunks = 32;
+__host__ __device__ __forceinline__ bool tail_seg_start(int cl) { return cl == 0; }
+__host__ __device__ __forceinline__ bool tail_seg_end(int cl, int nc) { return cl + 1 == nc; }
 static_assert(drain_period(2) * diag_bound(2) <= (1ll << 24) && drain_period(3) * diag_bound(3) <= (1ll << 24) &&
                   drain_period(4) * diag_bound(4) <= (1ll << 24) && drain_period(5) * diag_bound(5) <= (1ll << 24),
               "exact FP32 sums of the exact diagonals");
@@ -567,7 +565,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const uint64_t adesc0 = tc::sdesc_sw128(sA), bdesc0 = tc::sdesc_sw128(sB);
             constexpr FirstPassOrder<S> kFirst;
             bool ok = true;
-            int gc = 0, uc = 0, ts = 0;   // ts: tail segments committed
+            int gc = 0, uc = 0, ts = 0;   // ts: unit tails committed
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
                 int j0, z, c0, c1;
                 int64_t i0;
@@ -600,7 +598,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 if ((g == kEx - 1 || g == kEx) && gc >= 1 &&
                                     !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag, args.wait_ns))
                                     return false;
-                                // the tail of the previous segment must have been read
+                                // the tail of the previous unit must have been read
                                 if (g > kEx && seg0 && q == S && ts >= 1 &&
                                     !tc::mbar_wait(&tailEmpty, (ts - 1) & 1, &abort_flag, args.wait_ns)) return false;
                                 tc::fence_after();
@@ -610,7 +608,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             const uint64_t b0 =
                                 bdesc0 + (uint64_t)((b * kBSlice + (ri == 0 ? kBPart : 0)) >> 4);
                             // a fresh sum: every exact diagonal at its first pair
-                            // of the chunk, the tail at its first pair of a segment
+                            // of the chunk, the tail at its first pair of the unit
                             const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1 && cl % drain_period(g) == 0)
                                                           : (seg0 && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
@@ -684,7 +682,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         bool ok = true;
-        int gc = 0, ts = 0;                        // ts: tail segments read
+        int gc = 0, ts = 0;                        // ts: unit tails read
         int dn[kNEx] = {};                         // drains of each exact diagonal so far
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             int j0, z, c0, c1;
@@ -693,9 +691,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             long long Sx[kHalf];
 #pragma unroll
             for (int j = 0; j < kHalf; j++) Sx[j] = 0;
-            // the unit's outputs: row i, columns j0 + v < n; the FP32 tail of
-            // each is summed over the segments in its own slot of the raw
-            // partials (only this thread touches it; registers are full)
+            // the unit's outputs: row i, columns j0 + v < n; the FP32 tail goes
+            // to the raw partials straight from TMEM (registers are full)
             const int jn = args.n - j0;
             const int64_t i = i0 + row;
             float *Pt = (float *)args.P;
@@ -735,7 +732,6 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     // tail slot of column j0 + v: tb + v * (2 * kPartWords * M) floats
                     float *tb = Pt + 2 * part_word(z, args.n, j0, 2, args.M, i) + half;
                     const int64_t tstep = 2 * kPartWords * args.M;
-                    const bool seg_first = c - c0 < kTailSeg;   // the unit's first segment writes
 #pragma unroll 1
                     for (int h = 0; h < kHalf; h += 8) {
                         uint32_t r[8];
@@ -745,9 +741,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                             for (int v = 0; v < 8; v++) {
                                 if (h + v >= jn) break;
-                                float *t = tb + (h + v) * tstep;
-                                const float x = __uint_as_float(r[v]);
-                                *t = seg_first ? x : *t + x;
+                                tb[(h + v) * tstep] = __uint_as_float(r[v]);
                             }
                         }
                     }
@@ -919,13 +913,18 @@ bool make_map(CUtensorMap *m, void *base, uint64_t rows, uint64_t tiles, uint32_
 // complex output and split, at about one chunk per 6 us and 6 TB/s).  At
 // least 16 K chunks per split, partials within the workspace; 0 if even one
 // split does not fit.
+// K splits of a product: at least enough that no work unit spans more than
+// kUnitChunks K chunks (accuracy of the FP32 tail), then the count that
+// spreads the units best over the SMs, within the partials' memory.
 int choose_splits(int tiles, int nchunks, int n, int64_t M, size_t partial_bytes, int sms) {
     constexpr int64_t kPB = kPartWords * 8;       // bytes per complex output and split
     if ((int64_t)n * M * kPB > (int64_t)partial_bytes) return 0;
-    int best = 1;
+    const int sp0 = (nchunks + kUnitChunks - 1) / kUnitChunks;
+    if ((int64_t)sp0 * n * M * kPB > (int64_t)partial_bytes) return 0;
+    int best = sp0;
     double best_t = 1e30;
-    for (int sp = 1; sp <= 32; sp++) {
-        if ((int64_t)sp * 16 > nchunks && sp > 1) break;
+    for (int sp = sp0; sp <= sp0 + 32; sp++) {
+        if ((int64_t)sp * 16 > nchunks && sp > sp0) break;
         if ((int64_t)sp * n * M * kPB > (int64_t)partial_bytes) break;
         const int64_t u = (int64_t)tiles * sp;
         const int64_t per = (u + sms - 1) / sms;
@@ -948,7 +947,12 @@ size_t ozaki_a_bytes(int64_t N) {
 
 size_t ozaki_partial_bytes(int64_t N, int m) {
     const int mp = (m + kW - 1) / kW * kW;
-    return (size_t)N * (kPartWords * 8) * std::max<int64_t>(16 * kW, 8 * (int64_t)mp);
+    // splits x columns: the minimum split count of a product with K = N at
+    // full width, or 8 splits, or 16 tiles' worth for narrow products
+    const int64_t nch = ozaki_padded(N) / kKC;
+    const int64_t sp0 = (nch + kUnitChunks - 1) / kUnitChunks;
+    return (size_t)N * (kPartWords * 8) *
+           std::max<int64_t>(16 * kW, std::max<int64_t>(8, sp0) * (int64_t)mp);
 }
 
 size_t ozaki_b_bytes(int64_t N, int m) {

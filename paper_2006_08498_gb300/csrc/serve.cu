@@ -170,6 +170,7 @@ void worker(BseServer *S, int slot) {
         chase_opts o{};
         o.seed = rq.seed;
         o.degree_group = rq.degree_group;
+        o.nex_damping = rq.nex_damping;
         if (warm) {
             o.d_V0 = warm->d_evecs;
             o.ldv0 = N;

@@ -392,6 +392,25 @@ def test_precision_bf16x3_runs_as_mixed(ctx):
     assert b[3]["filter_matvecs_low"] > 0
 
 
+def test_solve_nex_tuner_matches_oracle(ctx, c1):
+    """nev = 50, nex = 10 with the nex tuner at a target damping of 0.75:
+    the same growth of nex as the oracle's tuner (to 20), the same eigenpairs
+    as the dense oracle, iterations within one of the oracle's and fewer
+    than with nex fixed."""
+    H, w, _ = c1
+    ref = oracle.chase(H, 50, 10, tol=1e-10, deg_max=36, nex_damping=0.75)
+    Hd = ctx.build_hamiltonian(0, 125, 4, 4)
+    e0, _, _, s0 = ctx.solve(Hd, 50, 10, tol=1e-10, deg_max=36)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 10, tol=1e-10, deg_max=36, nex_damping=0.75)
+    assert ref["nex"] == 20 and st["nex_used"] == 20 and s0["nex_used"] == 10
+    _check_solution(H, evals, host(Vd), resid, 50, w_exact=w, ref=ref["evecs"])
+    assert np.max(resid) <= 1e-10
+    assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[pkg.CHASE_FP64], atol=0)
+    assert abs(st["iters"] - ref["iters"]) <= 1 and st["iters"] < s0["iters"]
+    with pytest.raises(pkg.BseError):
+        ctx.solve(Hd, 50, 10, nex_damping=1.5)
+
+
 def test_solve_is_deterministic(ctx):
     Hd = ctx.build_hamiltonian(4, 30, 4, 4)
     a = ctx.solve(Hd, 30, 15)

@@ -331,3 +331,31 @@ def test_damping_matches_tables_s8_s9():
         for row in golden(table):
             lam, alpha, beta, inv_rho = float(row[1]), float(row[2]), float(row[3]), float(row[6])
             assert oracle.damping(lam, alpha, beta) == pytest.approx(inv_rho, abs=1.01e-5)
+
+
+def test_grown_nex_limits():
+    assert oracle.grown_nex(40, 100, 20000) == 80
+    assert oracle.grown_nex(3, 10, 1000) == 11
+    assert oracle.grown_nex(200, 300, 20000) == 212        # m <= 512
+    assert oracle.grown_nex(10, 40, 56) == 16              # m <= N
+
+
+def test_chase_nex_tuner():
+    """nev = 50, nex = 10 on the N = 2000 matrix: the settled damping of the
+    last wanted pair (about 0.81) exceeds a target of 0.75, so nex doubles
+    once; the solve reaches the dense eigenvalues in fewer iterations.  A
+    target above the damping changes nothing, bit for bit."""
+    H = oracle.build_h(0, 125, 4, 4)
+    w, _ = oracle.eigh(H, 0)
+    plain = oracle.chase(H, 50, 10, trace=True)
+    tuned = oracle.chase(H, 50, 10, nex_damping=0.75)
+    assert plain["nex"] == 10 and tuned["nex"] == 20
+    assert tuned["status"] == "ok" and tuned["iters"] < plain["iters"]
+    assert np.max(np.abs(tuned["evals"] - w[:50]) / np.abs(w[:50])) < 1e-10
+    assert np.max(tuned["resid"]) <= 1e-10
+    # the damping the tuner saw settles near the value of the exact spectrum
+    h = plain["history"][-1]
+    d_last = oracle.damping(h["theta"][50 - 1 - h["locked"]], h["theta"][-1], h["beta"])
+    assert d_last == pytest.approx(oracle.damping(w[49], w[59], h["beta"]), abs=0.01)
+    same = oracle.chase(H, 50, 10, nex_damping=0.99)
+    assert same["nex"] == 10 and np.array_equal(same["evals"], plain["evals"])
