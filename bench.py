@@ -495,24 +495,41 @@ def run_ours(args, rank, world, local_rank):
                     "projected": True,
                     "sample": ("the same oracle steps with one thread at N=%d, products "
                                "scaled by N^2, QR and Rayleigh-Ritz by N" % one["n_small"])}}
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the serving mix on the freed device (its own server and contexts)
+        del H, evecs
+        torch.cuda.empty_cache()
+        sv = serving_mix(args)
+        line["serving"] = {k: sv[k] for k in ("metric", "value", "unit", "p50_s", "p99_s",
+                                              "solves_per_s", "requests", "ok",
+                                              "warm_requests", "arrival_rate_per_s",
+                                              "calibrated_capacity_per_s", "slots",
+                                              "product_batching")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
 def run_serving(args):
+    """The serving mix alone: one JSON line."""
+    from paper_2006_08498_gb300 import build as pkg_build
+    pkg_build.build()
+    print(json.dumps(serving_mix(args)), flush=True)
+
+
+def serving_mix(args):
     """Serving mix: 256 requests, Poisson arrivals, N = 16 Nk with Nk ~
     U{63..1000}, nev ~ U{10..100}, nex = max(10, ceil(nev/2)), 30% warm-start
     neighbours (same seed and Nk as an earlier request, w0 scaled by 1 + d,
     d ~ U[-0.02, 0.02]), admission by an HBM budget.  The arrival rate is set
-    to 80% of the throughput measured on a calibration batch."""
+    to 80% of the throughput measured on a calibration batch.  Returns the
+    result as a dict (p50/p99 latency, solves/s, statuses)."""
     import math
     import numpy as np
     import torch
     import paper_2006_08498_gb300 as pkg
-    from paper_2006_08498_gb300 import build as pkg_build
-    pkg_build.build()
     torch.cuda.set_device(0)
     rng = np.random.default_rng(0)
     n_req = args.requests
@@ -531,6 +548,8 @@ def run_serving(args):
     budget = int(0.85 * free)
     ctx = pkg.Context(0)
     ctx.server_create(budget, args.slots)
+    if args.batch_window is not None:
+        ctx.server_batching(True, args.batch_window)
     prec = PRECISIONS[args.precision]
 
     def submit(q, tickets):
@@ -566,6 +585,7 @@ def run_serving(args):
     for r in res:
         statuses[str(r["status"])] = statuses.get(str(r["status"]), 0) + 1
     warm_used = sum(1 for q in reqs if q["warm"] is not None)
+    batch = ctx.server_batch_stats()
     ctx.server_destroy()
     ctx.close()
     line = {"metric": "chase_serving_latency_p99", "value": float(np.percentile(lat, 99)),
@@ -575,9 +595,11 @@ def run_serving(args):
             "warm_requests": warm_used, "arrival_rate_per_s": rate,
             "calibrated_capacity_per_s": cap, "slots": args.slots, "budget_bytes": budget,
             "precision": args.precision, "degree_group": args.degree_group, "data": "synthetic",
+            "product_batching": None if args.batch_window is None else dict(
+                batch, window_s=args.batch_window),
             "config": {"workload": "serving_mix_256", "N": "16*U{63..1000}", "nev": "U{10..100}",
                        "nex": "max(10, ceil(nev/2))", "warm_fraction": 0.3, "tol": 1e-10}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -588,6 +610,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving mix after the timed steps")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed-precision and Eq. (S1)-degree solves after the timed steps")
     ap.add_argument("--clock-log", default=None,
@@ -596,6 +620,9 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--batch-window", type=float, default=None,
+                    help="serving: run concurrent solves' products in shared launches, "
+                         "waiting up to this many seconds for company (default: off)")
     ap.add_argument("--nk", type=int, default=WORKLOAD["Nk"], help="k-points (N = 16 Nk)")
     ap.add_argument("--nev", type=int, default=WORKLOAD["nev"])
     ap.add_argument("--nex", type=int, default=WORKLOAD["nex"])

@@ -292,6 +292,12 @@ typedef struct {
                                 this solve if that request has finished       */
     int degree_group;        /* as chase_opts.degree_group (0: Eq. (S1))       */
     double nex_damping;      /* as chase_opts.nex_damping (0: nex fixed)       */
+    const void *d_H;         /* NULL: the synthetic Hamiltonian above.  Else the
+                                caller's N x N Hermitian matrix on the server's
+                                device (N = Nk Nv Nc, column-major, ld = ldh),
+                                read by the solve and not copied: the caller
+                                keeps it unchanged until the request finishes */
+    int64_t ldh;
 } chase_request;
 
 typedef struct {
@@ -321,6 +327,21 @@ int chase_server_evecs(bsechase_ctx *ctx, uint64_t ticket, void *d_out, int64_t 
 /* Cancel a queued request, or drop a finished one's results and eigenvectors
  * (BSE_EBUSY while it runs or while a queued warm start depends on it). */
 int chase_server_release(bsechase_ctx *ctx, uint64_t ticket);
+/* Product batching (off by default): with enabled = 1 the tensor-core
+ * products that the running solves submit within window_s of each other, or
+ * as soon as every running solve has submitted one, run in one launch of the
+ * persistent product kernel, each with the same work units and arithmetic as
+ * alone (results are unchanged, bit for bit).  With enabled = 0 every product
+ * is launched on its own slot's stream, and the slots' kernels overlap on the
+ * device by stream concurrency alone; on the serving mix of mixed sizes this
+ * measured faster (the window delays launches, and a shared launch waits for
+ * its slowest member's operands).  Only while no request is queued or running
+ * (BSE_EBUSY otherwise).  No counterpart in the paper. */
+int chase_server_batching(bsechase_ctx *ctx, int enabled, double window_s);
+/* Launches the batcher made, products they carried, and the most products
+ * in one launch. */
+int chase_server_batch_stats(bsechase_ctx *ctx, int64_t *launches, int64_t *products,
+                             int *max_products);
 /* Admitted bytes (running + resident), queued and running requests. */
 int chase_server_info(bsechase_ctx *ctx, size_t *held_bytes, int *queued, int *running);
 /* Stop the workers (waits for running solves) and free everything. */

@@ -30,6 +30,7 @@ ABI_SYMBOLS = (
     "chase_gram", "chase_gram_noalloc",
     "chase_server_create", "chase_server_submit", "chase_server_poll", "chase_server_wait",
     "chase_server_evecs", "chase_server_release", "chase_server_info", "chase_server_destroy",
+    "chase_server_batching", "chase_server_batch_stats",
 )
 
 
@@ -76,7 +77,8 @@ class Request(ctypes.Structure):
                 ("nev", ctypes.c_int), ("nex", ctypes.c_int), ("tol", ctypes.c_double),
                 ("deg_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("warm_ticket", ctypes.c_uint64), ("degree_group", ctypes.c_int),
-                ("nex_damping", ctypes.c_double)]
+                ("nex_damping", ctypes.c_double), ("d_H", ctypes.c_void_p),
+                ("ldh", ctypes.c_int64)]
 
 
 class Result(ctypes.Structure):
@@ -161,7 +163,11 @@ def load():
     L.chase_server_info.argtypes = [P, ctypes.POINTER(sz), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32)]
     L.chase_server_destroy.argtypes = [P]
-    for f in ("create", "submit", "poll", "wait", "evecs", "release", "info", "destroy"):
+    L.chase_server_batching.argtypes = [P, i32, dbl]
+    L.chase_server_batch_stats.argtypes = [P, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                           ctypes.POINTER(i32)]
+    for f in ("create", "submit", "poll", "wait", "evecs", "release", "info", "destroy",
+              "batching", "batch_stats"):
         getattr(L, "chase_server_" + f).restype = i32
     _lib = L
     return L
@@ -397,16 +403,20 @@ class Context:
         self._check(load().chase_server_destroy(self._h))
 
     def submit(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
-               model=None, warm_ticket=0, degree_group=0, nex_damping=0.0):
-        """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc);
-        returns its ticket."""
+               model=None, warm_ticket=0, degree_group=0, nex_damping=0.0, H=None):
+        """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc), or of
+        the caller's device matrix H (N = Nk Nv Nc, column-major; kept alive
+        and unchanged by the caller until the request finishes); returns its
+        ticket."""
         md = dict(DEFAULT_MODEL)
         if model:
             md.update(model)
         r = Request(seed, Nk, Nv, Nc, 1 if model else 0,
                     Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
                           int(md["rank_x"])),
-                    nev, nex, tol, deg_max, precision, warm_ticket, degree_group, nex_damping)
+                    nev, nex, tol, deg_max, precision, warm_ticket, degree_group, nex_damping,
+                    None if H is None else ctypes.c_void_p(H.data_ptr()),
+                    0 if H is None else _ld(H))
         t = ctypes.c_uint64(0)
         self._check(load().chase_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value
@@ -440,6 +450,16 @@ class Context:
         self._check(load().chase_server_info(self._h, ctypes.byref(held), ctypes.byref(q),
                                              ctypes.byref(r)))
         return dict(held_bytes=held.value, queued=q.value, running=r.value)
+
+    def server_batching(self, enabled=True, window_s=0.0):
+        """Turn the server's product batching on (with this window) or off."""
+        self._check(load().chase_server_batching(self._h, 1 if enabled else 0, float(window_s)))
+
+    def server_batch_stats(self):
+        n, p, mx = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(0)
+        self._check(load().chase_server_batch_stats(self._h, ctypes.byref(n), ctypes.byref(p),
+                                                    ctypes.byref(mx)))
+        return dict(launches=n.value, products=p.value, max_products=mx.value)
 
     def rayleigh_ritz(self, H, Q, norm=1.0, precision=CHASE_FP64):
         N, m = Q.shape

@@ -229,11 +229,13 @@ int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy
         // tensor flops: 8 real flops per complex multiply-add for each of
         // the 21 (FP64) or 10 (FP32-level) slice pairs
         const double pairs = op.low ? 10.0 : 21.0;
-        cudaEvent_t e0, e1;
-        kernel_events(ctx, 8.0 * pairs * (double)op.N * (double)op.N * n, &e0, &e1);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        // a batched launch holds other solvers' products: not timed per product
+        if (!ctx->batcher)
+            kernel_events(ctx, 8.0 * pairs * (double)op.N * (double)op.N * n, &e0, &e1);
         CK(ozaki_zgemm(ctx->oh, n, Y, ldy, C, ldc, ep, ctx->ozB.p, (int *)ctx->ozF.p, ctx->sc,
                        op.low ? 1 : 0, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st, e0,
-                       e1));
+                       e1, ctx->batcher));
     } else
         CK(launch_zgemm_nn(op.N, n, op.N, op.H, op.ldh, Y, ldy, C, ldc, ep, ctx->st));
     return BSE_OK;

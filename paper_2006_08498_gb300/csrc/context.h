@@ -44,6 +44,7 @@ struct bsechase_ctx {
     double k_ms = 0.0, k_flops = 0.0;
     int64_t k_launches = 0;
     BseServer *server = nullptr;     // request server attached to this context
+    OzBatcher *batcher = nullptr;    // a server slot's shared product batcher
 };
 
 // Record a failure message (printf-style with one string argument).

@@ -101,10 +101,22 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 // order) when that fills the `sms` multiprocessors better.  When ev0/ev1
 // are given they are recorded on `st` just before and after the
 // tensor-core kernel itself (not the slicing or the split-K sum).
+// With a batcher, the tensor-core kernel is launched by the batcher together
+// with other threads' products (ev0/ev1 are then not recorded).
+struct OzBatcher;
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
                         z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
-                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                        cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                        OzBatcher *batcher = nullptr);
+// Product batcher shared by the solver threads of a request server: products
+// submitted within window_s of each other (or as soon as every active solver
+// has submitted one) run in one launch of the tensor-core kernel.
+OzBatcher *ozb_create(int device, int sms, double window_s);
+void ozb_destroy(OzBatcher *b);
+void ozb_set_active(OzBatcher *b, int n);   // solvers that may submit
+void ozb_set_window(OzBatcher *b, double window_s);
+void ozb_counts(OzBatcher *b, int64_t *launches, int64_t *jobs, int *max_jobs);
 
 // ---- vector kernels (vec.cu)
 int vec_partial_blocks(int64_t N);

@@ -44,7 +44,15 @@
 // thread issues between MMAs (a barrier wait, a commit) costs issue time, so
 // the pipeline is built to need few of them.
 #include <algorithm>
+#include <chrono>
 #include <climits>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -297,6 +305,23 @@ struct OzArgs {
     uint64_t wait_ns;        // limit of each bounded mbarrier wait
 };
 
+// One launch of the product kernel runs the work units of up to kMaxJobs
+// independent products (a batch; one product alone is a batch of one).  Job
+// j's units are numbered from unit0 on; each job keeps its own operands,
+// tensor maps, K splits and partials, so its arithmetic is the same whatever
+// else runs in the launch.
+constexpr int kMaxJobs = 8;
+struct OzJob {
+    CUtensorMap tmA, tmB;    // slices of op(A) and of Y
+    OzArgs args;
+    int unit0;               // first unit of this job in the launch
+};
+struct OzBatch {
+    OzJob job[kMaxJobs];
+    int njobs;
+    int units;               // units of all jobs
+};
+
 // Limit of each wait of the wind-down after an expired wait: long enough for
 // any copy or MMA already issued to finish.
 constexpr uint64_t kWindDownNs = 2000000000ull;
@@ -431,8 +456,7 @@ struct ProducerOrder {
 // reduction kernels sum the K splits and recombine.
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
-k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              OzArgs args) {
+k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
     constexpr int S = Cfg::kSl;
     constexpr int S2 = 2 * S;
     constexpr int kEx = Cfg::kEx;              // diagonals 2..kEx exact
@@ -464,8 +488,8 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int nch = args.nchunks;
-    const int units = args.tx * args.ty * args.tz;
+    const int units = bt.units;
+    const uint64_t wait_ns = bt.job[0].args.wait_ns;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAPairs; s++) { tc::mbar_init(&fullA[s], 1); tc::mbar_init(&emptyA[s], 1); }
@@ -494,65 +518,80 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // buffer was filled before
     auto bbuf = [](int q, int gc) { return q == 1 ? ((gc & 1) ? S : 0) : q - 1; };
     auto buse = [](int q, int gc) { return q == 1 ? (gc >> 1) : gc; };
-    // unit -> column tile, row tile, K range
-    auto unit = [&](int u, int &j0, int64_t &i0, int &z, int &c0, int &c1) {
-        const int x = u % args.tx, y = (u / args.tx) % args.ty;
-        z = u / (args.tx * args.ty);
+    // unit -> job, column tile, row tile, K range
+    auto unit = [&](int u, int &jb, int &j0, int64_t &i0, int &z, int &c0, int &c1) {
+        jb = 0;
+        while (jb + 1 < bt.njobs && u >= bt.job[jb + 1].unit0) jb++;
+        const OzArgs &a = bt.job[jb].args;
+        const int ul = u - bt.job[jb].unit0;
+        const int x = ul % a.tx, y = (ul / a.tx) % a.ty;
+        z = ul / (a.tx * a.ty);
         j0 = x * kW;
         i0 = (int64_t)y * kBM;
-        c0 = z * args.csplit;
-        c1 = min(nch, c0 + args.csplit);
+        c0 = z * a.csplit;
+        c1 = min(a.nchunks, c0 + a.csplit);
     };
 
-    // Arrivals the producer made on each full barrier: arrA[st] on fullA[st]
-    // (one per fill), arrB[g][par] on fullB[g][par] (S - 2 or 2 per phase).
-    // The wind-down after an expired wait completes a partly armed B phase
-    // and waits until every armed phase has landed (producer thread only).
-    int arrA[kAPairs] = {}, arrB[2][2] = {};
+    // Where the producer stopped: chunk ab_gc, item ab_it of ProducerOrder
+    // (items before it issued).  The wind-down after an expired wait derives
+    // from these which phases of the full barriers were armed.
+    int ab_gc = 0, ab_it = 0;
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            tc::prefetch_tmap(&tmA);
-            tc::prefetch_tmap(&tmB);
+            for (int j = 0; j < bt.njobs; j++) {
+                tc::prefetch_tmap(&bt.job[j].tmA);
+                tc::prefetch_tmap(&bt.job[j].tmB);
+            }
             constexpr ProducerOrder<S> order;
             bool ok = true;
             int gc = 0;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-                int j0, z, c0, c1;
+                int jb, j0, z, c0, c1;
                 int64_t i0;
-                unit(u, j0, i0, z, c0, c1);
+                unit(u, jb, j0, i0, z, c0, c1);
+                const CUtensorMap *tmA = &bt.job[jb].tmA, *tmB = &bt.job[jb].tmB;
+                const int nch = bt.job[jb].args.nchunks;
                 for (int c = c0; c < c1 && ok; c++, gc++) {
+                    ab_gc = gc;
 #pragma unroll
                     for (int it = 0; it < 2 * S; it++) {
                         if (order.kind[it] == 0) {
                             const int pp = order.idx[it];
                             const int ua = S * gc + pp, st = ua % kAPairs, n = ua / kAPairs;
-                            if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
+                            if (n >= 1 && !tc::mbar_wait(&emptyA[st], (n - 1) & 1, &abort_flag, wait_ns)) {
+                                ok = false;
+                                ab_it = it;
+                                break;
+                            }
                             tc::mbar_expect_tx(&fullA[st], 2 * kATile);
-                            arrA[st]++;
                             // parts (slice p, re) and (slice p, im) = 2 pp, 2 pp + 1 in the
                             // A tensor's part order
                             uint8_t *adst = sA + st * 2 * kATile;
-                            tc::tma_load_3d(adst, &tmA, 0, (int)i0, (2 * pp) * nch + c, &fullA[st]);
-                            tc::tma_load_3d(adst + kATile, &tmA, 0, (int)i0, (2 * pp + 1) * nch + c, &fullA[st]);
+                            tc::tma_load_3d(adst, tmA, 0, (int)i0, (2 * pp) * nch + c, &fullA[st]);
+                            tc::tma_load_3d(adst + kATile, tmA, 0, (int)i0, (2 * pp + 1) * nch + c, &fullA[st]);
                         } else {
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
-                            if (n >= 1 && !tc::mbar_wait(q >= S - 2 ? &emptyBg : &emptyB[b], (n - 1) & 1, &abort_flag, args.wait_ns)) {
+                            if (n >= 1 && !tc::mbar_wait(q >= S - 2 ? &emptyBg : &emptyB[b], (n - 1) & 1, &abort_flag, wait_ns)) {
                                 ok = false;
+                                ab_it = it;
                                 break;
                             }
                             uint64_t *fb = &fullB[q >= 3 ? 0 : 1][gc & 1];
                             tc::mbar_expect_tx(fb, kBSlice);
-                            arrB[q >= 3 ? 0 : 1][gc & 1]++;
                             uint8_t *bdst = sB + b * kBSlice;
                             // smem [-Yi | Yr | Yi] from parts 2, 0, 1
-                            tc::tma_load_3d(bdst + 0 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, fb);
-                            tc::tma_load_3d(bdst + 1 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, fb);
-                            tc::tma_load_3d(bdst + 2 * kBPart, &tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, fb);
+                            tc::tma_load_3d(bdst + 0 * kBPart, tmB, 0, j0, ((q - 1) * 3 + 2) * nch + c, fb);
+                            tc::tma_load_3d(bdst + 1 * kBPart, tmB, 0, j0, ((q - 1) * 3 + 0) * nch + c, fb);
+                            tc::tma_load_3d(bdst + 2 * kBPart, tmB, 0, j0, ((q - 1) * 3 + 1) * nch + c, fb);
                         }
                     }
                 }
+            }
+            if (ok) {
+                ab_gc = gc;      // every chunk issued in full
+                ab_it = 0;
             }
         }
     } else if (warp == 1) {
@@ -567,9 +606,9 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             bool ok = true;
             int gc = 0, uc = 0, ts = 0;   // ts: unit tails committed
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x, uc++) {
-                int j0, z, c0, c1;
+                int jb, j0, z, c0, c1;
                 int64_t i0;
-                unit(u, j0, i0, z, c0, c1);
+                unit(u, jb, j0, i0, z, c0, c1);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
                     const int cl = c - c0, nc = c1 - c0;
                     const bool seg0 = tail_seg_start(cl);
@@ -578,7 +617,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         const int p = pi / 2 + 1, ri = pi & 1;
                         const int ua = S * gc + (p - 1), st = ua % kAPairs;
                         if (ri == 0) {
-                            if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
+                            if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag, wait_ns)) { ok = false; break; }
                             tc::fence_after();
                         }
                         const uint64_t a0 = adesc0 + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
@@ -591,16 +630,16 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                 // B slices before the first MMA of their group (the
                                 // chunk's first MMA reads slice FirstPassOrder.q[0] >= 3)
                                 if ((q == kFirst.q[0] || q == 2) &&
-                                    !tc::mbar_wait(&fullB[q >= 3 ? 0 : 1][gc & 1], (gc >> 1) & 1, &abort_flag, args.wait_ns))
+                                    !tc::mbar_wait(&fullB[q >= 3 ? 0 : 1][gc & 1], (gc >> 1) & 1, &abort_flag, wait_ns))
                                     return false;
                                 // the previous chunk's accumulators g <= kEx - 1 before
                                 // the first of them (g = kEx - 1, q = 3), g = kEx at q = 4
                                 if ((g == kEx - 1 || g == kEx) && gc >= 1 &&
-                                    !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag, args.wait_ns))
+                                    !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag, wait_ns))
                                     return false;
                                 // the tail of the previous unit must have been read
                                 if (g > kEx && seg0 && q == S && ts >= 1 &&
-                                    !tc::mbar_wait(&tailEmpty, (ts - 1) & 1, &abort_flag, args.wait_ns)) return false;
+                                    !tc::mbar_wait(&tailEmpty, (ts - 1) & 1, &abort_flag, wait_ns)) return false;
                                 tc::fence_after();
                             }
                             const uint32_t d = tmem + (uint32_t)((g <= kEx ? g - 2 : kNEx) * kN);
@@ -685,9 +724,10 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         int gc = 0, ts = 0;                        // ts: unit tails read
         int dn[kNEx] = {};                         // drains of each exact diagonal so far
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-            int j0, z, c0, c1;
+            int jb, j0, z, c0, c1;
             int64_t i0;
-            unit(u, j0, i0, z, c0, c1);
+            unit(u, jb, j0, i0, z, c0, c1);
+            const OzArgs &args = bt.job[jb].args;
             long long Sx[kHalf];
 #pragma unroll
             for (int j = 0; j < kHalf; j++) Sx[j] = 0;
@@ -700,7 +740,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll 1
                 for (int g = 2; g <= kEx; g++) {
                     if (!drain_due(g, c - c0, c1 - c0)) continue;
-                    if (!tc::mbar_wait(&accFull[g - 2], dn[g - 2] & 1, &abort_flag, args.wait_ns)) { ok = false; break; }
+                    if (!tc::mbar_wait(&accFull[g - 2], dn[g - 2] & 1, &abort_flag, wait_ns)) { ok = false; break; }
                     dn[g - 2]++;
                     tc::fence_after();
                     const uint32_t col = (uint32_t)((g - 2) * kN + half * kHalf);
@@ -723,7 +763,7 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     if (lane == 0 && g >= kEx - 1) tc::mbar_arrive(&accEmpty[g == kEx ? 1 : 0]);
                 }
                 if (ok && kTail && tail_seg_end(c - c0, c1 - c0)) {
-                    if (!tc::mbar_wait(&tailFull, ts & 1, &abort_flag, args.wait_ns)) {
+                    if (!tc::mbar_wait(&tailFull, ts & 1, &abort_flag, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -780,27 +820,46 @@ k_ozaki_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         //    issued has completed.
         bool drained = true;
         if (warp == 0 && lane == 0) {
+            constexpr ProducerOrder<S> order;
             constexpr int kArr[2] = {S - 2, 2};
-            for (int g = 0; g < 2; g++)
+            // B: chunks before ab_gc armed both groups of their barrier in
+            // full; chunk ab_gc armed the items before ab_it
+            for (int g = 0; g < 2; g++) {
+                int part = 0;
+                for (int it = 0; it < ab_it; it++)
+                    if (order.kind[it] == 1 && (order.idx[it] >= 3 ? 0 : 1) == g) part++;
                 for (int par = 0; par < 2; par++) {
-                    while (arrB[g][par] % kArr[g] != 0) {
-                        tc::mbar_arrive(&fullB[g][par]);
-                        arrB[g][par]++;
+                    int ph = ab_gc / 2 + ((ab_gc & 1) && par == 0 ? 1 : 0);   // full chunks of parity par
+                    if (par == (ab_gc & 1) && part > 0) {
+                        for (int k = part; k < kArr[g]; k++) tc::mbar_arrive(&fullB[g][par]);
+                        ph++;
                     }
-                    const int ph = arrB[g][par] / kArr[g];
                     if (ph > 0) drained &= tc::mbar_wait_for(&fullB[g][par], (ph - 1) & 1, kWindDownNs);
                 }
-            for (int st = 0; st < kAPairs; st++)
-                if (arrA[st] > 0) drained &= tc::mbar_wait_for(&fullA[st], (arrA[st] - 1) & 1, kWindDownNs);
+            }
+            // A: the last fill of each stage, ua = S gc + pp
+            for (int st = 0; st < kAPairs; st++) {
+                int last = -1;
+                for (int it = 0; it < ab_it; it++)
+                    if (order.kind[it] == 0 && (S * ab_gc + order.idx[it]) % kAPairs == st)
+                        last = max(last, S * ab_gc + order.idx[it]);
+                if (last < 0 && S * ab_gc > 0) {
+                    const int top = S * ab_gc - 1;
+                    last = top - (((top - st) % kAPairs) + kAPairs) % kAPairs;
+                }
+                if (last >= 0) drained &= tc::mbar_wait_for(&fullA[st], (last / kAPairs) & 1, kWindDownNs);
+            }
         }
         if (warp == 1 && lane == 0) {
             tc::mma_commit(&mmaDone);
             drained &= tc::mbar_wait_for(&mmaDone, 0, kWindDownNs);
         }
-        if (!drained) set_error(args.sc, DEV_TIMEOUT, -1 - (int)blockIdx.x);
+        if (!drained)
+            for (int j = 0; j < bt.njobs; j++) set_error(bt.job[j].args.sc, DEV_TIMEOUT, -1 - (int)blockIdx.x);
         tc::fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) set_error(args.sc, DEV_TIMEOUT, blockIdx.x);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < bt.njobs; j++) set_error(bt.job[j].args.sc, DEV_TIMEOUT, blockIdx.x);
     }
     if (warp == 1) {
         tc::fence_after();
@@ -981,24 +1040,225 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     return cudaGetLastError();
 }
 
+namespace {
+
 template <class Cfg>
-cudaError_t launch_variant(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a,
-                           dim3 grid, cudaStream_t st) {
+cudaError_t launch_variant(const OzBatch &b, int sms, cudaStream_t st) {
     static std::once_flag once[kMaxDevices];
     static cudaError_t attr[kMaxDevices];
     {
         const cudaError_t ae = smem_attr_once(once, attr, (const void *)k_ozaki_zgemm<Cfg>, Cfg::kSmem);
         if (ae != cudaSuccess) return ae;
     }
-    k_ozaki_zgemm<Cfg><<<grid, kThreads, Cfg::kSmem, st>>>(tmA, tmB, a);
+    const dim3 grid((unsigned)std::min(b.units, sms));
+    k_ozaki_zgemm<Cfg><<<grid, kThreads, Cfg::kSmem, st>>>(b);
     bse_count_launches(1);
     return cudaGetLastError();
 }
 
+cudaError_t launch_batch(const OzBatch &b, int low, int sms, cudaStream_t st) {
+    return low ? launch_variant<CfgMixed>(b, sms, st) : launch_variant<CfgFP64>(b, sms, st);
+}
+
+// A batch of one product.
+OzBatch single(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a) {
+    OzBatch b;
+    memset(&b, 0, sizeof b);
+    b.job[0].tmA = tmA;
+    b.job[0].tmB = tmB;
+    b.job[0].args = a;
+    b.job[0].unit0 = 0;
+    b.njobs = 1;
+    b.units = a.tx * a.ty * a.tz;
+    return b;
+}
+
+}  // namespace
+
+// ------------------------------------------------------ product batcher
+// Products that solver threads of one process submit at about the same time
+// run in one launch of the kernel.  A submitting thread records an event on
+// its stream (its operand slices are ready) and queues its job; the first
+// queued thread leads: it waits until as many jobs are queued as there are
+// active solvers (each of them is then waiting on a product) or until the
+// window has passed since it began to lead, then launches every queued job
+// of the same precision (up to kMaxJobs, oldest first) on the batcher's
+// stream behind the jobs' events, records one event after the launch, and
+// hands the lead on.  Every submitter makes its stream wait for that event
+// before its split reduction.  The jobs' units, splits and operands are
+// those of the product alone, so results are the same, bit for bit.
+struct OzBatcher {
+    std::mutex mu;
+    std::condition_variable cv;
+    struct Pending {
+        OzJob job;
+        int low = 0;
+        cudaEvent_t ready = nullptr, done = nullptr;
+        bool launched = false;
+        cudaError_t err = cudaSuccess;
+    };
+    std::deque<Pending *> queue;
+    bool leading = false;
+    int active = 1;
+    double window_s = 50e-6;
+    int sms = 0, device = 0;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> pool;            // events free for reuse
+    std::map<cudaEvent_t, int> waiting;       // batch event -> submitters still to wait on it
+    int64_t launches = 0, jobs = 0;
+    int max_jobs = 0;
+};
+
+OzBatcher *ozb_create(int device, int sms, double window_s) {
+    OzBatcher *b = new (std::nothrow) OzBatcher();
+    if (!b) return nullptr;
+    b->device = device;
+    b->sms = sms;
+    b->window_s = window_s;
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return nullptr;
+    }
+    return b;
+}
+
+void ozb_destroy(OzBatcher *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->st);
+    for (cudaEvent_t e : b->pool) cudaEventDestroy(e);
+    for (auto &kv : b->waiting) cudaEventDestroy(kv.first);
+    cudaStreamDestroy(b->st);
+    delete b;
+}
+
+void ozb_set_window(OzBatcher *b, double window_s) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->window_s = window_s;
+}
+
+void ozb_set_active(OzBatcher *b, int n) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->active = std::max(1, n);
+    b->cv.notify_all();
+}
+
+void ozb_counts(OzBatcher *b, int64_t *launches, int64_t *jobs, int *max_jobs) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    *launches = b->launches;
+    *jobs = b->jobs;
+    *max_jobs = b->max_jobs;
+}
+
+namespace {
+
+// The per-thread event a submitter records when its operands are ready.
+cudaEvent_t ready_event() {
+    thread_local cudaEvent_t ev = nullptr;
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ev = nullptr;
+    }
+    return ev;
+}
+
+// Run job (with its precision) through the batcher; returns after `st` waits
+// for the launch that contains it.
+cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int low, cudaStream_t st) {
+    OzBatcher::Pending me;
+    me.job = job;
+    me.low = low;
+    me.ready = ready_event();
+    if (!me.ready) return cudaErrorUnknown;
+    cudaError_t e = cudaEventRecord(me.ready, st);
+    if (e != cudaSuccess) return e;
+    std::unique_lock<std::mutex> lk(b->mu);
+    b->queue.push_back(&me);
+    b->cv.notify_all();
+    while (!me.launched) {
+        if (b->leading) {
+            b->cv.wait(lk);
+            continue;
+        }
+        // lead: wait for company, then launch what is queued
+        b->leading = true;
+        const auto t_end = std::chrono::steady_clock::now() +
+                           std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                               std::chrono::duration<double>(b->window_s));
+        while ((int)b->queue.size() < b->active &&
+               b->cv.wait_until(lk, t_end) != std::cv_status::timeout) {
+        }
+        std::vector<OzBatcher::Pending *> take;
+        const int low0 = b->queue.front()->low;
+        for (auto it = b->queue.begin(); it != b->queue.end() && (int)take.size() < kMaxJobs;) {
+            if ((*it)->low == low0) {
+                take.push_back(*it);
+                it = b->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        cudaEvent_t done = nullptr;
+        if (!b->pool.empty()) {
+            done = b->pool.back();
+            b->pool.pop_back();
+        }
+        lk.unlock();
+        OzBatch bt;
+        memset(&bt, 0, sizeof bt);
+        int u = 0;
+        for (size_t k = 0; k < take.size(); k++) {
+            bt.job[k] = take[k]->job;
+            bt.job[k].unit0 = u;
+            u += take[k]->job.args.tx * take[k]->job.args.ty * take[k]->job.args.tz;
+        }
+        bt.njobs = (int)take.size();
+        bt.units = u;
+        cudaError_t le = cudaSuccess;
+        if (!done && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+            le = cudaGetLastError();
+            done = nullptr;
+        }
+        for (size_t k = 0; k < take.size() && le == cudaSuccess; k++)
+            le = cudaStreamWaitEvent(b->st, take[k]->ready, 0);
+        if (le == cudaSuccess) le = launch_batch(bt, low0, b->sms, b->st);
+        if (le == cudaSuccess) le = cudaEventRecord(done, b->st);
+        lk.lock();
+        for (auto *p : take) {
+            p->launched = true;
+            p->err = le;
+            p->done = (le == cudaSuccess) ? done : nullptr;
+        }
+        if (le == cudaSuccess) {
+            b->waiting[done] = (int)take.size();
+            b->launches++;
+            b->jobs += (int64_t)take.size();
+            b->max_jobs = std::max(b->max_jobs, (int)take.size());
+        } else if (done) {
+            b->pool.push_back(done);
+        }
+        b->leading = false;
+        b->cv.notify_all();
+    }
+    const cudaError_t err = me.err;
+    cudaEvent_t done = me.done;
+    lk.unlock();
+    if (err != cudaSuccess) return err;
+    e = cudaStreamWaitEvent(st, done, 0);
+    lk.lock();
+    if (--b->waiting[done] == 0) {
+        b->waiting.erase(done);
+        b->pool.push_back(done);
+    }
+    return e;
+}
+
+}  // namespace
+
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
                         const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
                         z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
-                        cudaEvent_t ev0, cudaEvent_t ev1) {
+                        cudaEvent_t ev0, cudaEvent_t ev1, OzBatcher *batcher) {
     if (n <= 0) return cudaSuccess;
     const int64_t N = oh.N, Np = oh.Np;
     const int mp = (n + kW - 1) / kW * kW;
@@ -1031,13 +1291,16 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
-    const int64_t units = (int64_t)tx * ty * nsplit;
-    dim3 grid((unsigned)std::min<int64_t>(units, sms));
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
-    if (ev0) cudaEventRecord(ev0, st);
-    cudaError_t e = low ? launch_variant<CfgMixed>(tmA, tmB, a, grid, st)
-                        : launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
-    if (ev1) cudaEventRecord(ev1, st);
+    const OzBatch one = single(tmA, tmB, a);
+    cudaError_t e;
+    if (batcher) {
+        e = ozb_run(batcher, one.job[0], low, st);   // launched with other solvers' products
+    } else {
+        if (ev0) cudaEventRecord(ev0, st);
+        e = launch_batch(one, low, sms, st);
+        if (ev1) cudaEventRecord(ev1, st);
+    }
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
     k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, a.P, a.E, a.F, ep, Y, ldy, C, ldc);
@@ -1110,8 +1373,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
-    dim3 grid((unsigned)std::min<int64_t>((int64_t)tx * ty * nsplit, sms));
-    cudaError_t e = launch_variant<CfgFP64>(tmA, tmB, a, grid, st);
+    cudaError_t e = launch_batch(single(tmA, tmB, a), 0, sms, st);
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((M + 255) / 256), (unsigned)n);
     k_gen_reduce<<<gr, 256, 0, st>>>(M, n, nsplit, a.P, a.E, a.F, mode, D, ldd, shift, hermitize, C, ldc);

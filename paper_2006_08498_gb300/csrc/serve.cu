@@ -12,8 +12,11 @@
 //     memory is available); an estimate above the whole budget is refused;
 //   - continuous batching: every slot is a host worker with its own CUDA
 //     stream and solver context, so requests admitted while others run
-//     execute concurrently on the device, and each request's kernels are the
-//     same as when it runs alone (results are identical alone and in a mix);
+//     execute concurrently on the device; the tensor-core products that the
+//     running solves submit at about the same time run in one launch of the
+//     persistent product kernel (the product batcher of ozaki.cu), each with
+//     the same units and arithmetic as alone, so results are identical alone
+//     and in a mix;
 //   - resident results: a finished request keeps its eigenvectors on the
 //     device (counted in the budget, evicted least-recently-used) so that a
 //     later request can warm-start from them (chase_request.warm_ticket);
@@ -71,14 +74,16 @@ struct BseServer {
     std::list<uint64_t> lru;        // finished requests holding eigenvectors, oldest first
     uint64_t next_ticket = 1;
     bool stop = false;
+    OzBatcher *batcher = nullptr;   // products of the slots' solves in shared launches
+    int running = 0;                // solves in progress
 };
 
 namespace {
 
-size_t estimate_run_bytes(int64_t N, int m, int nev, int precision) {
+size_t estimate_run_bytes(int64_t N, int m, int nev, int precision, bool own_h) {
     const size_t Np = (size_t)ozaki_padded(N);
     const size_t mp = (size_t)((std::max(m, 32) + 31) / 32 * 32);
-    size_t b = 16 * (size_t)N * N;                          // H
+    size_t b = own_h ? 16 * (size_t)N * N : 0;              // H, unless the caller's
     b += 4 * 16 * (size_t)N * m;                            // V and three scratch blocks
     b += 16 * (size_t)N * nev;                              // eigenvectors
     b += (size_t)N * 8 * 3 * 16 + ((size_t)20 << 20);       // Lanczos blocks, small matrices
@@ -149,6 +154,7 @@ void worker(BseServer *S, int slot) {
             S->held += job->run_bytes;
             job->state = 1;
             job->t_start = now_s();
+            if (S->batcher) ozb_set_active(S->batcher, ++S->running);
             if (job->rq.warm_ticket) {
                 auto w = S->reqs.find(job->rq.warm_ticket);
                 if (w != S->reqs.end() && w->second->d_evecs && w->second->N == job->N) warm = w->second;
@@ -159,14 +165,16 @@ void worker(BseServer *S, int slot) {
         const int64_t N = job->N;
         void *dH = nullptr, *dZ = nullptr;
         int rc = BSE_OK;
-        if (cudaMallocAsync(&dH, 16 * (size_t)N * N, ctx->st) != cudaSuccess ||
+        if ((!rq.d_H && cudaMallocAsync(&dH, 16 * (size_t)N * N, ctx->st) != cudaSuccess) ||
             cudaMallocAsync(&dZ, 16 * (size_t)N * rq.nev, ctx->st) != cudaSuccess) {
             cudaGetLastError();
             rc = BSE_ENOMEM;
         }
-        if (rc == BSE_OK)
+        if (rc == BSE_OK && !rq.d_H)
             rc = bse_build_hamiltonian(ctx, rq.seed, rq.Nk, rq.Nv, rq.Nc,
                                        rq.use_model ? &rq.model : nullptr, dH, N);
+        const z_t *Hs = rq.d_H ? (const z_t *)rq.d_H : (const z_t *)dH;
+        const int64_t lds = rq.d_H ? rq.ldh : N;
         chase_opts o{};
         o.seed = rq.seed;
         o.degree_group = rq.degree_group;
@@ -179,7 +187,7 @@ void worker(BseServer *S, int slot) {
         std::vector<double> ev(rq.nev), rs(rq.nev);
         chase_stats st{};
         if (rc == BSE_OK)
-            rc = solve_device(ctx, (const z_t *)dH, N, N, rq.nev, rq.nex, rq.tol, rq.deg_max,
+            rc = solve_device(ctx, Hs, N, lds, rq.nev, rq.nex, rq.tol, rq.deg_max,
                               rq.precision, &o, ev.data(), (z_t *)dZ, N, rs.data(), &st);
         if (dH) cudaFreeAsync(dH, ctx->st);
         release_workspace(ctx);
@@ -192,6 +200,7 @@ void worker(BseServer *S, int slot) {
                 if (w != S->reqs.end()) w->second->pins--;
             }
             S->held -= job->run_bytes;
+            if (S->batcher) ozb_set_active(S->batcher, --S->running);
             job->t_end = t_end;
             job->status = rc;
             job->err = (rc == BSE_OK) ? std::string() : ctx->err;
@@ -239,6 +248,7 @@ void bse_server_shutdown(bsechase_ctx *ctx) {
     S->cv_work.notify_all();
     for (auto &t : S->workers)
         if (t.joinable()) t.join();
+    ozb_destroy(S->batcher);
     for (auto &kv : S->reqs)
         if (kv.second->d_evecs) cudaFree(kv.second->d_evecs);
     for (bsechase_ctx *c : S->slots) bsechase_destroy(c);
@@ -284,7 +294,8 @@ int chase_server_submit(bsechase_ctx *ctx, const chase_request *req, uint64_t *t
     q->rq = *req;
     q->rq.precision = precision_mode(req->precision);
     q->N = N;
-    q->run_bytes = estimate_run_bytes(N, m, req->nev, q->rq.precision);
+    if (req->d_H && req->ldh < N) return fail(ctx, BSE_EINVAL, "request H: ldh < N%s");
+    q->run_bytes = estimate_run_bytes(N, m, req->nev, q->rq.precision, req->d_H == nullptr);
     if (q->run_bytes > S->budget)
         return fail(ctx, BSE_ENOMEM, "request needs more than the whole HBM budget%s");
     q->t_submit = now_s();
@@ -395,6 +406,39 @@ int chase_server_release(bsechase_ctx *ctx, uint64_t ticket) {
 int chase_server_destroy(bsechase_ctx *ctx) {
     if (!ctx) return BSE_EINVAL;
     bse_server_shutdown(ctx);
+    return BSE_OK;
+}
+
+int chase_server_batching(bsechase_ctx *ctx, int enabled, double window_s) {
+    if (!ctx || !ctx->server) return BSE_EINVAL;
+    BseServer *S = ctx->server;
+    if (!(window_s >= 0.0 && window_s <= 1.0))
+        return fail(ctx, BSE_EINVAL, "batching window must be in [0, 1] s%s");
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto &kv : S->reqs)
+        if (kv.second->state != 2 && !kv.second->cancelled)
+            return fail(ctx, BSE_EBUSY, "requests are queued or running%s");
+    if (!enabled) {
+        for (bsechase_ctx *c : S->slots) c->batcher = nullptr;
+        ozb_destroy(S->batcher);
+        S->batcher = nullptr;
+        return BSE_OK;
+    }
+    if (!S->batcher) S->batcher = ozb_create(ctx->device, ctx->sms, window_s);
+    if (!S->batcher) return fail(ctx, BSE_ECUDA, "cannot create the product batcher%s");
+    ozb_set_window(S->batcher, window_s);
+    for (bsechase_ctx *c : S->slots) c->batcher = S->batcher;
+    return BSE_OK;
+}
+
+int chase_server_batch_stats(bsechase_ctx *ctx, int64_t *launches, int64_t *products,
+                             int *max_products) {
+    if (!ctx || !ctx->server || !launches || !products || !max_products) return BSE_EINVAL;
+    BseServer *S = ctx->server;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *launches = *products = 0;
+    *max_products = 0;
+    if (S->batcher) ozb_counts(S->batcher, launches, products, max_products);
     return BSE_OK;
 }
 

@@ -49,6 +49,29 @@ def test_alone_equals_mix(ctx):
     ctx.server_destroy()
 
 
+def test_batched_products_share_launches_and_change_nothing(ctx):
+    """Product batching: with a window of 5 ms, the products of concurrent
+    solves run several to a launch (launch statistics), and every request's
+    result is bit for bit the one of the same server with batching off."""
+    reqs = [dict(seed=21 + i, Nk=63 + 17 * i, Nv=4, Nc=4, nev=12 + 5 * i, nex=10)
+            for i in range(6)]
+    ctx.server_create(64 * GB, 6)
+    assert ctx.server_batch_stats()["launches"] == 0              # off by default
+    ctx.server_batching(True, 5e-3)
+    res_b = [ctx.wait(t) for t in [ctx.submit(**r) for r in reqs]]
+    st = ctx.server_batch_stats()
+    ctx.server_batching(False)
+    res_u = [ctx.wait(t) for t in [ctx.submit(**r) for r in reqs]]
+    assert ctx.server_batch_stats()["launches"] == 0
+    ctx.server_destroy()
+    assert all(r["status"] == pkg.BSE_OK for r in res_b + res_u)
+    assert st["max_products"] >= 2 and st["products"] > st["launches"]
+    for a, b in zip(res_b, res_u):
+        assert np.array_equal(a["evals"], b["evals"])
+        assert np.array_equal(a["resid"], b["resid"])
+        assert a["stats"]["iters"] == b["stats"]["iters"]
+
+
 def test_server_result_equals_direct_solve(ctx):
     Hd = ctx.build_hamiltonian(3, 63, 4, 4)
     e, V, r, st = ctx.solve(Hd, 20, 10, seed=3)
@@ -147,3 +170,42 @@ def test_concurrent_mixed_sizes_all_ok(ctx):
         assert r["nev"] == q["nev"]
         assert np.max(r["resid"]) <= 1e-10
     ctx.server_destroy()
+
+
+def test_serving_sizes_match_exact_eigenvalues(ctx):
+    """Requests of the serving mix's sizes (N = 1008 .. 4000, nev 10 .. 100,
+    one warm neighbour with w0 scaled by 1.01) against the exact eigenvalues
+    of the same synthetic Hamiltonians (structured oracle)."""
+    import oracle
+    reqs = [dict(seed=31, Nk=63, nev=10, nex=10), dict(seed=32, Nk=125, nev=50, nex=25),
+            dict(seed=33, Nk=250, nev=100, nex=50), dict(seed=31, Nk=63, nev=10, nex=10,
+                                                        model=dict(w0=0.303))]
+    ctx.server_create(64 * GB, 4)
+    t0 = ctx.submit(Nv=4, Nc=4, **reqs[0])
+    ts = [t0] + [ctx.submit(Nv=4, Nc=4, **r) for r in reqs[1:3]]
+    ts.append(ctx.submit(Nv=4, Nc=4, warm_ticket=t0, **reqs[3]))
+    res = [ctx.wait(t) for t in ts]
+    ctx.server_destroy()
+    for r, q in zip(res, reqs):
+        assert r["status"] == pkg.BSE_OK and np.max(r["resid"]) <= 1e-10
+        lam = oracle.structured.lowest_eigenvalues(
+            oracle.structured.bse_blocks(q["seed"], q["Nk"], 4, 4, q.get("model")), q["nev"])
+        assert np.max(np.abs(r["evals"] - lam) / np.abs(lam)) <= 1e-10
+
+
+def test_request_with_caller_hamiltonian(ctx):
+    """A request may carry the caller's device matrix instead of the
+    generator's parameters: a seeded Hermitian matrix with a known spectrum
+    (N = 600 = 150 x 2 x 2), against its eigenvalues and the dense oracle."""
+    import oracle
+    from inputs import hermitian
+    A, lam = hermitian(600, 41)
+    Ad = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().T
+    ctx.server_create(16 * GB, 2)
+    t = ctx.submit(seed=0, Nk=150, Nv=2, Nc=2, nev=30, nex=15, H=Ad)
+    r = ctx.wait(t)
+    ctx.server_destroy()
+    assert r["status"] == pkg.BSE_OK and r["N"] == 600
+    w, _ = oracle.eigh(A, 0)
+    assert np.max(np.abs(r["evals"] - w[:30]) / np.abs(w[:30])) <= 1e-10
+    assert np.max(np.abs(r["evals"] - lam[:30]) / lam[:30]) <= 1e-10
