@@ -383,16 +383,20 @@ def run_ours(args, rank, world, local_rank):
     clocks = Clocks(local_rank, args.clock_log.replace("{rank}", str(local_rank)) if args.clock_log else None)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.synchronize()
     ev0.record(stream)
     stats, stats_evals = [], []
-    for _ in range(args.steps):
+    for k in range(args.steps):
+        evs[k].record(stream)
         out = step()
         stats.append(out[3])
         stats_evals.append(out[0])
+    evs[args.steps].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     if dist:
         dist.barrier()
     ck = clocks.stop()
@@ -463,6 +467,8 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(W, precision=args.precision, degree_group=args.degree_group,
                            parallelism="replicas" if world > 1 else "single"),
             "throughput_solves_per_s": replica_throughput(world, args.steps, ms_max),
+            "step_ms": {"mean": statistics.mean(step_ms), "min": min(step_ms),
+                        "std": statistics.pstdev(step_ms), "n": len(step_ms)},
             "solve": {k: st[k] for k in ("iters", "matvecs", "filter_matvecs",
                                          "filter_matvecs_low", "filter_launches", "ms_lanczos",
                                          "ms_filter", "ms_qr", "ms_rr", "ms_resid",
