@@ -361,8 +361,6 @@ __host__ __device__ constexpr int drain_period(int g) { return g <= 3 ? 2 : 1; }
 // at a tolerance of 1e-10 (N = 50000); over 2048 of K it is about 5e-12 and
 // the solve takes the oracle's 8 iterations.
 constexpr int kUnitChunks = 32;
-__host__ __device__ __forceinline__ bool tail_seg_start(int cl) { return cl == 0; }
-__host__ __device__ __forceinline__ bool tail_seg_end(int cl, int nc) { return cl + 1 == nc; }
 static_assert(drain_period(2) * diag_bound(2) <= (1ll << 24) && drain_period(3) * diag_bound(3) <= (1ll << 24) &&
                   drain_period(4) * diag_bound(4) <= (1ll << 24) && drain_period(5) * diag_bound(5) <= (1ll << 24),
               "exact FP32 sums of the exact diagonals");
@@ -611,7 +609,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                 unit(u, jb, j0, i0, z, c0, c1);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
                     const int cl = c - c0, nc = c1 - c0;
-                    const bool seg0 = tail_seg_start(cl);
+                    const bool first = cl == 0;   // the unit's first chunk
 #pragma unroll
                     for (int pi = 0; pi < S2; pi++) {
                         const int p = pi / 2 + 1, ri = pi & 1;
@@ -638,7 +636,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                                     !tc::mbar_wait(&accEmpty[g == kEx ? 1 : 0], (gc - 1) & 1, &abort_flag, wait_ns))
                                     return false;
                                 // the tail of the previous unit must have been read
-                                if (g > kEx && seg0 && q == S && ts >= 1 &&
+                                if (g > kEx && first && q == S && ts >= 1 &&
                                     !tc::mbar_wait(&tailEmpty, (ts - 1) & 1, &abort_flag, wait_ns)) return false;
                                 tc::fence_after();
                             }
@@ -649,7 +647,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                             // a fresh sum: every exact diagonal at its first pair
                             // of the chunk, the tail at its first pair of the unit
                             const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1 && cl % drain_period(g) == 0)
-                                                          : (seg0 && pi == 0 && q == S);
+                                                          : (first && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
                             const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
                             if (pi == 0 && coll == tc::A_FILL)
@@ -706,7 +704,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                         }
                     }
                     // the chunk's last MMA is a tail pair (p = S, q = 1)
-                    if (ok && kTail && tail_seg_end(cl, nc)) {
+                    if (ok && kTail && cl + 1 == nc) {
                         tc::mma_commit(&tailFull);
                         ts++;
                     }
@@ -762,7 +760,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                     __syncwarp();
                     if (lane == 0 && g >= kEx - 1) tc::mbar_arrive(&accEmpty[g == kEx ? 1 : 0]);
                 }
-                if (ok && kTail && tail_seg_end(c - c0, c1 - c0)) {
+                if (ok && kTail && c + 1 == c1) {
                     if (!tc::mbar_wait(&tailFull, ts & 1, &abort_flag, wait_ns)) {
                         ok = false;
                         break;
