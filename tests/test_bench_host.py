@@ -31,10 +31,19 @@ def test_clock_summary_without_samples():
 
 
 def test_traffic_record_matches_workload_only():
-    d = bench._traffic("fp64", "chase_N20000_nev100_nex40")
+    d = bench._traffic("fp64", bench.WORKLOAD["workload"])
     with open(os.path.join(ROOT, "profiles", "filter_traffic_fp64.txt")) as f:
         rec = json.load(f)
     assert d == rec
-    assert d["bytes_per_launch"] > 9.69e9             # at least the slices of H
-    assert bench._traffic("fp64", "chase_N50000_nev200_nex80") is None
-    assert bench._traffic("nonexistent", "chase_N20000_nev100_nex40") is None
+    Np = 50048
+    assert d["bytes_per_launch"] > 24 * Np * Np       # at least the slices of H
+    assert bench._traffic("fp64", "chase_N20000_nev100_nex40") is None
+    assert bench._traffic("nonexistent", bench.WORKLOAD["workload"]) is None
+
+
+def test_projected_solve_time():
+    """cpu_baseline projection: build + per-column product time x products +
+    iterations x (QR + Rayleigh-Ritz)."""
+    smp = dict(t_build=4.0, t_mv=0.05, t_qr=1.0, t_rr=0.5)
+    assert bench.project_solve(smp, dict(iters=8, matvecs=47231)) == \
+        4.0 + 0.05 * 47231 + 8 * 1.5
