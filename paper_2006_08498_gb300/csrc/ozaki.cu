@@ -432,13 +432,15 @@ struct ProducerOrder {
 };
 
 // A persistent kernel: one CTA per SM walks the work units u = blockIdx.x,
-// blockIdx.x + gridDim.x, ...  A unit is 128 rows x kW complex columns of C
-// over the K chunks of one split, numbered column tile fastest, then row
-// tile, then split (so the CTAs running at one time share the operand slices
-// of one K range in L2).  TMEM, the barriers and the pipelines live for the
-// whole launch: the next unit's loads and MMAs start while the previous one
-// drains, and no SM waits between CTAs.  Every role counts the chunks it has
-// processed (gc) and the units (uc), and all barrier phases follow from them.
+// blockIdx.x + gridDim.x, ... of a batch of products (usually one).  A unit
+// is 128 rows x kW complex columns of one product's C over the K chunks of
+// one split (at most kUnitChunks), numbered job by job, and within a job
+// column tile fastest, then row tile, then split (so the CTAs running at one
+// time share the operand slices of one K range in L2).  TMEM, the barriers
+// and the pipelines live for the whole launch: the next unit's loads and MMAs
+// start while the previous one drains, and no SM waits between CTAs.  Every
+// role counts the chunks it has processed (gc) and the units' tails (ts), and
+// all barrier phases follow from them.
 //
 // Per K chunk the MMA warp runs 2S passes, (p, Re H) then (p, Im H) for
 // p = 1..S, and in each pass the slices q = S+1-p down to 1 of Y (the first
