@@ -13,8 +13,10 @@ is needed between steps.
 After the timed steps the line adds: one end-to-end solve through the
 host-buffer entry point (H copied in, eigenvectors copied out); one solve
 in the mixed precision mode with its per-eigenpair differences from the
-FP64 solve; one solve with the degrees of Eq. (S1) unchanged; and the CPU
-oracle timed on the host's cores on a bounded sample of the same workload.
+FP64 solve; one solve with the degrees of Eq. (S1) unchanged; one solve
+with H generated straight into its tensor-core slices (never stored); the
+CPU oracle timed on the host's cores on a bounded sample of the same
+workload; and the serving mix.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch under torch.distributed.run: every rank solves its own
@@ -453,7 +455,24 @@ def run_ours(args, rank, world, local_rank):
         (ev_0, V_0, r_0, st_0), t_0 = timed(precision=prec, degree_group=0)
         extras["degree_group_0"] = {"value": t_0, "unit": UNIT, "iters": st_0["iters"],
                                     "matvecs": st_0["matvecs"], "max_resid": float(np.max(r_0))}
-        del V_0, V_ref
+        del V_0
+        # the same solve with H generated straight into its tensor-core slices
+        # (chase_solve_bse: the 16 N^2 bytes of H are never stored); generator
+        # included, like the timed step
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev_h, V_h, r_h, st_h = ctx.solve_bse(replica_seed(W["seed"], rank), W["Nk"], W["Nv"],
+                                             W["Nc"], nev, nex, tol=W["tol"],
+                                             deg_max=W["deg_max"], precision=prec,
+                                             degree_group=args.degree_group)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extras["h_not_stored"] = {
+            "value": e0.elapsed_time(e1) / 1e3, "unit": UNIT, "iters": st_h["iters"],
+            "device_bytes_not_stored": 16 * N * N,
+            "same_bits_as_stored_h": bool(np.array_equal(ev_h, ev_ref) and
+                                          torch.equal(V_h, V_ref))}
+        del V_h, V_ref
 
     if rank == 0:
         st = stats[-1]

@@ -199,6 +199,21 @@ int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int 
                 double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
                 void *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
 
+/* As chase_solve for the synthetic Hamiltonian of bse_build_hamiltonian
+ * (same seed, Nk, Nv, Nc, model), without storing it: its elements are
+ * generated straight into the tensor-core slices of H, so the N x N
+ * complex128 matrix (16 N^2 bytes) never exists and the device memory the
+ * solve needs drops from 40 N^2 to 24 N^2 bytes plus workspace (Sec. 3's
+ * filter works on H only through its products).  The slices, and so every
+ * result, are bit for bit those of bse_build_hamiltonian + chase_solve.
+ * Tensor-core precisions only (CHASE_FP64, CHASE_MIXED_FP32, value 2);
+ * CHASE_FP64_DFMA needs the stored H: BSE_EINVAL.  Other errors as
+ * chase_solve. */
+int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
+                    const bse_model *model, int nev, int nex, double tol, int deg_max,
+                    int precision, const chase_opts *opts, double *h_evals, void *d_evecs,
+                    int64_t ldz, double *h_resid, chase_stats *stats);
+
 /* As chase_solve with every matrix in HOST memory: h_H (N x N) is copied to
  * a context-owned device buffer and the eigenvectors are copied back into
  * h_evecs (N x nev, ld = ldz).  Host buffers should be pinned for full

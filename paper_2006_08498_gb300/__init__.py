@@ -25,7 +25,7 @@ CHASE_FP64, CHASE_MIXED_FP32, CHASE_MIXED_BF16X3, CHASE_FP64_DFMA = 0, 1, 2, 3
 ABI_SYMBOLS = (
     "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
     "bsechase_set_wait_limit",
-    "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host",
+    "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host", "chase_solve_bse",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
     "chase_gram", "chase_gram_noalloc",
     "chase_server_create", "chase_server_submit", "chase_server_poll", "chase_server_wait",
@@ -138,6 +138,9 @@ def load():
     L.chase_solve.restype = i32
     L.chase_solve_host.argtypes = L.chase_solve.argtypes
     L.chase_solve_host.restype = i32
+    L.chase_solve_bse.argtypes = [P, u64, i32, i32, i32, ctypes.POINTER(Model), i32, i32, dbl, i32,
+                                  i32, ctypes.POINTER(Opts), DP, P, i64, DP, ctypes.POINTER(Stats)]
+    L.chase_solve_bse.restype = i32
     L.chase_lanczos.argtypes = [P, P, i64, i64, i32, i32, i32, u64, i32, DP]
     L.chase_lanczos.restype = i32
     L.chase_filter.argtypes = [P, P, i64, i64, P, i64, i32, ctypes.POINTER(ctypes.c_int),
@@ -320,6 +323,36 @@ class Context:
                                 ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
                                 ctypes.byref(st))
         self._check(rc, (BSE_OK, BSE_ENOCONV) if allow_noconv else (BSE_OK,))
+        d = st.as_dict()
+        d["status"] = rc
+        return evals, evecs, resid, d
+
+    def solve_bse(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
+                  model=None, deg_init=20, max_iter=50, lanczos_steps=25, lanczos_vecs=4,
+                  seed_start=0, evecs=None, degree_group=0, nex_damping=0.0):
+        """Lowest nev eigenpairs of the synthetic Hamiltonian (seed, Nk, Nv,
+        Nc, model) without storing it (chase_solve_bse).  seed_start seeds the
+        Lanczos and start vectors (`seed` of solve()).  Returns (evals, evecs
+        tensor N x nev, resid, stats)."""
+        torch = self._torch
+        N = Nk * Nv * Nc
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        if evecs is None:
+            evecs = colmajor_empty(N, nev, device=torch.device("cuda", self.device))
+        md = dict(DEFAULT_MODEL)
+        if model:
+            md.update(model)
+        mdl = Model(md["band_gap"], md["w0"], md["x0"], md["jitter"], md["dispersion"],
+                    int(md["rank_x"]))
+        st = Stats()
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed_start, None,
+                       degree_group, nex_damping)
+        rc = load().chase_solve_bse(self._h, seed, Nk, Nv, Nc, ctypes.byref(mdl), nev, nex, tol,
+                                    deg_max, precision, ctypes.byref(o), _dp(evals),
+                                    ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
+                                    ctypes.byref(st))
+        self._check(rc)
         d = st.as_dict()
         d["status"] = rc
         return evals, evecs, resid, d

@@ -179,6 +179,7 @@ struct Hop {
     int64_t N, ldh;
     bool tc;         // tensor-core emulation
     bool low = false;  // FP32-level accuracy (mixed precision filter)
+    const BseSource *bse = nullptr;   // H not stored: its slices from the generator
 };
 
 int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
@@ -199,7 +200,11 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
     ctx->oh.wait_ns = ctx->wait_ns;
-    CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
+    if (op.bse)
+        CK(ozaki_prepare_bse(op.bse->Nk, op.bse->Nv, op.bse->Nc, op.bse->md, op.bse->dE, op.bse->u,
+                             op.bse->a, op.bse->Kt, &ctx->oh, ctx->sc, ctx->st));
+    else
+        CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
     return BSE_OK;
 }
 
@@ -498,7 +503,8 @@ constexpr double kNexSettled = 0.02;   // consecutive dampings this close: settl
 
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
-                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats) {
+                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats,
+                 const BseSource *bse) {
     int rc;
     int m = nev + nex;
     chase_opts o{};
@@ -538,6 +544,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     tm.mark(0);
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     Hop op{H, N, ldh, precision_uses_tc(precision)};
+    op.bse = bse;
     if ((rc = hop_prepare(ctx, op, m_cap))) return rc;
     GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
@@ -727,6 +734,38 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace {
+
+BseModel model_of(const bse_model *model) {
+    BseModel md{2.0, 0.3, 0.5, 0.01, 1.0, 8};
+    if (model) {
+        md.band_gap = model->band_gap;
+        md.w0 = model->w0;
+        md.x0 = model->x0;
+        md.jitter = model->jitter;
+        md.dispersion = model->dispersion;
+        md.rank_x = model->rank_x;
+    }
+    return md;
+}
+
+// The generator's tables in the context's workspace: u[N] and a[N R] first
+// (16-byte aligned), then dE[N] and Kt[Nk/2 + 1].
+int bse_tables(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+               BseSource *src) {
+    const int64_t N = (int64_t)Nk * Nv * Nc;
+    const size_t tb = (size_t)N * (1 + std::max(md.rank_x, 1)) * sizeof(z_t) +
+                      ((size_t)N + Nk / 2 + 1) * sizeof(double);
+    int rc;
+    if ((rc = ensure(ctx, ctx->tables, tb))) return rc;
+    z_t *u = (z_t *)ctx->tables.p, *a = u + N;
+    double *dE = (double *)(a + N * std::max(md.rank_x, 1)), *Kt = dE + N;
+    *src = BseSource{Nk, Nv, Nc, md, dE, Kt, u, a};
+    return BSE_OK;
+}
+
+}  // namespace
+
 // =================================================================== ABI
 
 extern "C" {
@@ -818,27 +857,41 @@ int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int 
     if (!ctx) return BSE_EINVAL;
     const int64_t N = bse_dim(Nk, Nv, Nc);
     if (N < 1 || !d_H || ldh < N) return fail(ctx, BSE_EINVAL, "bad sizes or NULL H%s");
-    BseModel md{2.0, 0.3, 0.5, 0.01, 1.0, 8};
-    if (model) {
-        md.band_gap = model->band_gap;
-        md.w0 = model->w0;
-        md.x0 = model->x0;
-        md.jitter = model->jitter;
-        md.dispersion = model->dispersion;
-        md.rank_x = model->rank_x;
-    }
+    const BseModel md = model_of(model);
     if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
     DeviceGuard g(ctx->device);
     int rc;
-    // u[N] and a[N R] first (16-byte aligned), then dE[N] and Kt[Nk/2 + 1]
-    const size_t tb = (size_t)N * (1 + std::max(md.rank_x, 1)) * sizeof(z_t) +
-                      ((size_t)N + Nk / 2 + 1) * sizeof(double);
-    if ((rc = ensure(ctx, ctx->tables, tb))) return rc;
-    z_t *u = (z_t *)ctx->tables.p, *a = u + N;
-    double *dE = (double *)(a + N * std::max(md.rank_x, 1)), *Kt = dE + N;
-    CK(launch_bse_build(seed, Nk, Nv, Nc, md, dE, u, a, Kt, (z_t *)d_H, ldh, ctx->st));
+    BseSource t;
+    if ((rc = bse_tables(ctx, seed, Nk, Nv, Nc, md, &t))) return rc;
+    CK(launch_bse_build(seed, Nk, Nv, Nc, md, (double *)t.dE, (z_t *)t.u, (z_t *)t.a,
+                        (double *)t.Kt, (z_t *)d_H, ldh, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     return BSE_OK;
+}
+
+int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
+                    const bse_model *model, int nev, int nex, double tol, int deg_max,
+                    int precision, const chase_opts *opts, double *h_evals, void *d_evecs,
+                    int64_t ldz, double *h_resid, chase_stats *stats) {
+    if (!ctx) return BSE_EINVAL;
+    const int64_t N = bse_dim(Nk, Nv, Nc);
+    if (N < 1) return fail(ctx, BSE_EINVAL, "bad sizes%s");
+    const BseModel md = model_of(model);
+    if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
+    if (!h_evals || !d_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
+    // the checks of chase_solve, with the (absent) matrix's place taken by an output
+    int rc = validate_solve(ctx, h_evals, N, N, nev, nex, tol, deg_max, precision, ldz);
+    if (rc) return rc;
+    if (!precision_uses_tc(precision_mode(precision)))
+        return fail(ctx, BSE_EINVAL, "the stored-H-free solve needs a tensor-core precision%s");
+    DeviceGuard g(ctx->device);
+    ctx->err.clear();
+    BseSource src;
+    if ((rc = bse_tables(ctx, seed, Nk, Nv, Nc, md, &src))) return rc;
+    CK(launch_bse_tables(seed, Nk, Nv, Nc, md, (double *)src.dE, (z_t *)src.u, (z_t *)src.a,
+                         (double *)src.Kt, ctx->st));
+    return solve_device(ctx, nullptr, N, N, nev, nex, tol, deg_max, precision_mode(precision),
+                        opts, h_evals, (z_t *)d_evecs, ldz, h_resid, stats, &src);
 }
 
 int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int nev, int nex,

@@ -52,10 +52,20 @@ int fail(bsechase_ctx *c, int code, const char *fmt, const char *detail = "");
 // Grow / free the context's workspace (stream-ordered on ctx->st).
 int ensure(bsechase_ctx *ctx, DevBuf &b, size_t bytes);
 void release_workspace(bsechase_ctx *ctx);
-// The whole solve on device buffers (chase_solve without argument checks).
+// The synthetic Hamiltonian as the solve's operator without H stored: its
+// parameters and the generator's tables (tensor-core precisions only).
+struct BseSource {
+    int Nk, Nv, Nc;
+    BseModel md;
+    const double *dE, *Kt;
+    const z_t *u, *a;
+};
+// The whole solve on device buffers (chase_solve without argument checks);
+// with `bse` set, H is that source's and `H` is unused.
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
                  double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
-                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats);
+                 z_t *d_evecs, int64_t ldz, double *h_resid, chase_stats *stats,
+                 const BseSource *bse = nullptr);
 // Whether `precision` is a chase_precision value, and the mode it runs
 // (CHASE_MIXED_BF16X3 runs as CHASE_MIXED_FP32).
 bool precision_valid(int precision);

@@ -17,7 +17,10 @@
 // triangle, each written in place and conjugated at its mirror, so H is
 // Hermitian bit for bit and every column is written with coalesced stores.
 // HBM traffic: 16 N^2 bytes.
+#include <algorithm>
+
 #include "common.cuh"
+#include "gen_element.cuh"
 #include "kernels.h"
 
 namespace {
@@ -86,27 +89,12 @@ bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ d
     }
     __syncthreads();
     const bool diag = ti == tj;
-    const int I = i0 + tx, kI = I / nb, bI = I % nb;
+    const int I = i0 + tx;
     for (int c = ty; c < kGT; c += 8) {
         if (diag && tx < c) continue;            // above the diagonal: the mirror pass
         const int J = j0 + c;
-        z_t x = zmk(0.0, 0.0);                   // sum_r a_Ir conj(a_Jr)
-        for (int r = 0; r < R; r++) {
-            const z_t ai = sai[r * kGT + tx], aj = saj[r * kGT + c];
-            x.x = fma(ai.x, aj.x, x.x);
-            x.x = fma(ai.y, aj.y, x.x);
-            x.y = fma(ai.y, aj.x, x.y);
-            x.y = fma(-ai.x, aj.y, x.y);
-        }
-        x = zscale(x, 2.0);
-        z_t w = zmk(0.0, 0.0);
-        if (bI == J % nb) {
-            int dk = kI - J / nb;
-            if (dk < 0) dk = -dk;
-            if (Nk - dk < dk) dk = Nk - dk;
-            w = zscale(zmul(ui[tx], zconj(uj[c])), md.w0 * Kt[dk]);
-        }
-        const z_t h = (I == J) ? zmk(dEi[tx] + x.x - w.x, 0.0) : zsub(x, w);
+        const z_t h = bse_element(I, J, R, sai + tx, saj + c, kGT, ui[tx], uj[c], dEi[tx], Nk, nb,
+                                  md.w0, Kt);
         tile[c][tx] = h;
         if (I < N && J < N) H[I + (int64_t)J * ldh] = h;
     }
@@ -121,12 +109,21 @@ bse_tile_kernel(int Nk, int nb, int N, BseModel md, const double *__restrict__ d
 
 }  // namespace
 
+cudaError_t launch_bse_tables(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+                              double *dE, z_t *u, z_t *a, double *Kt, cudaStream_t st) {
+    const int64_t N = (int64_t)Nk * Nv * Nc;
+    const int64_t n = std::max<int64_t>(N, Nk / 2 + 1);
+    bse_tables_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(seed, Nk, Nv, Nc, md, dE, u, a, Kt);
+    bse_count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
                              double *dE, z_t *u, z_t *a, double *Kt, z_t *H, int64_t ldh,
                              cudaStream_t st) {
     const int64_t N = (int64_t)Nk * Nv * Nc;
-    bse_tables_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(seed, Nk, Nv, Nc, md, dE, u, a, Kt);
-    bse_count_launches(1);
+    cudaError_t e = launch_bse_tables(seed, Nk, Nv, Nc, md, dE, u, a, Kt, st);
+    if (e != cudaSuccess) return e;
     const unsigned T = (unsigned)((N + kGT - 1) / kGT);
     const int dyn = 2 * kGT * md.rank_x * (int)sizeof(z_t);
     static std::once_flag once[kMaxDevices];

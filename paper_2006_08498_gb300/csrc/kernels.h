@@ -12,7 +12,10 @@ struct BseModel {
 
 // ---- generator (gen.cu)
 // Tables (device scratch): dE[N], u[N] = e^{i theta}, a[N * rank_x] and
-// Kt[Nk / 2 + 1] = 1 / (d^2 + 1/2).
+// Kt[Nk / 2 + 1] = 1 / (d^2 + 1/2).  launch_bse_tables writes the tables
+// alone; launch_bse_build writes them and then H.
+cudaError_t launch_bse_tables(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+                              double *dE, z_t *u, z_t *a, double *Kt, cudaStream_t st);
 cudaError_t launch_bse_build(uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
                              double *dE, z_t *u, z_t *a, double *Kt, z_t *H, int64_t ldh,
                              cudaStream_t st);
@@ -90,6 +93,13 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
                        const z_t *B, int64_t ldb, int mode, const z_t *D, int64_t ldd,
                        double shift, int hermitize, z_t *C, int64_t ldc, const OzGemmWork &w,
                        ChaseScalars *sc, int sms, cudaStream_t st);
+// The slices of the synthetic Hamiltonian generated from the generator's
+// tables (launch_bse_tables) without storing H; oh->A and oh->E must hold
+// ozaki_a_bytes(N) and Np ints.  The values are those bse_build_hamiltonian
+// writes, bit for bit.
+cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const double *dE,
+                              const z_t *u, const z_t *a, const double *Kt, OzakiH *oh,
+                              ChaseScalars *sc, cudaStream_t st);
 // Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
 cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
                             cudaStream_t st);

@@ -55,6 +55,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gen_element.cuh"
 #include "kernels.h"
 #include "tc_common.cuh"
 
@@ -287,6 +288,130 @@ __global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__res
         B[tiled_index(q * 3 + 0, k, j, Np, mp)] = bf16_exact(slice_value(tr[q], q));
         B[tiled_index(q * 3 + 1, k, j, Np, mp)] = bf16_exact(slice_value(ti[q], q));
         B[tiled_index(q * 3 + 2, k, j, Np, mp)] = bf16_exact(slice_value(-ti[q], q));
+    }
+}
+
+// ------------------------------- slices of the synthetic H, H not stored
+// The synthetic Hamiltonian's elements generated straight into the slices of
+// H (bse_element, the generator's own element function, so the values are
+// bit for bit those of bse_build_hamiltonian): the N x N complex128 matrix is
+// never stored.  Two passes over the lower-triangle 32 x 32 tiles of the
+// padded Np x Np matrix: the row exponents (each element counts for its row
+// and, conjugated, for its column's row), then the slices of every tile and
+// of its mirror.  The tables (dE, u = e^{i theta}, a, Kt) come from the
+// generator's table pass.
+constexpr int kGT = 32;
+
+// Stage the a rows, u and dE of the tile's rows i0.. and columns j0..
+__device__ __forceinline__ void stage_tile(int i0, int j0, int N, int R, const z_t *__restrict__ a,
+                                           const z_t *__restrict__ u, const double *__restrict__ dE,
+                                           z_t *sai, z_t *saj, z_t *ui, z_t *uj, double *dEi) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int e = ty * kGT + tx; e < kGT * R; e += kGT * 8) {
+        const int t = e / R, r = e % R;
+        sai[r * kGT + t] = (i0 + t < N) ? a[(int64_t)(i0 + t) * R + r] : zmk(0.0, 0.0);
+        saj[r * kGT + t] = (j0 + t < N) ? a[(int64_t)(j0 + t) * R + r] : zmk(0.0, 0.0);
+    }
+    if (ty == 0) {
+        ui[tx] = (i0 + tx < N) ? u[i0 + tx] : zmk(0.0, 0.0);
+        uj[tx] = (j0 + tx < N) ? u[j0 + tx] : zmk(0.0, 0.0);
+        dEi[tx] = (i0 + tx < N) ? dE[i0 + tx] : 0.0;
+    }
+}
+
+// Row exponents: E[i] = frexp exponent of max_k max(|Re H_ik|, |Im H_ik|).
+__global__ void __launch_bounds__(256)
+k_gen_row_exponent(int Nk, int nb, int N, BseModel md, const double *__restrict__ dE,
+                   const z_t *__restrict__ u, const z_t *__restrict__ a,
+                   const double *__restrict__ Kt, int *E, ChaseScalars *sc) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (ti < tj) return;
+    extern __shared__ z_t gsm[];
+    __shared__ z_t ui[kGT], uj[kGT];
+    __shared__ double dEi[kGT];
+    __shared__ unsigned long long rmax[kGT], cmax[kGT];
+    const int R = md.rank_x;
+    z_t *sai = gsm, *saj = gsm + kGT * R;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = ti * kGT, j0 = tj * kGT;
+    if (ty == 0) rmax[tx] = cmax[tx] = 0ull;
+    stage_tile(i0, j0, N, R, a, u, dE, sai, saj, ui, uj, dEi);
+    __syncthreads();
+    const int I = i0 + tx;
+    unsigned long long mine = 0;
+    for (int c = ty; c < kGT; c += 8) {
+        const int J = j0 + c;
+        if ((ti == tj && tx < c) || I >= N || J >= N) continue;
+        const z_t h = bse_element(I, J, R, sai + tx, saj + c, kGT, ui[tx], uj[c], dEi[tx], Nk, nb,
+                                  md.w0, Kt);
+        const unsigned long long mb = max(abs_bits(h.x), abs_bits(h.y));
+        mine = max(mine, mb);
+        atomicMax(&cmax[c], mb);                   // row J of H holds conj(h)
+    }
+    atomicMax(&rmax[tx], mine);
+    __syncthreads();
+    if (ty == 0) {
+        const unsigned long long m[2] = {rmax[tx], cmax[tx]};
+        const int row[2] = {i0 + tx, j0 + tx};
+        for (int k = 0; k < 2; k++) {
+            if (row[k] >= N || m[k] == 0) continue;
+            if (m[k] >= kNonFinite) set_error(sc, DEV_NONFINITE, row[k]);
+            else atomicMax(&E[row[k]], frexp_bits(m[k]));
+        }
+    }
+}
+
+// Slices of the tile (rows i0.., columns j0..) and of its mirror (rows j0..,
+// columns i0.., conjugated), in the layout of k_slice_h; zeros outside N.
+__global__ void __launch_bounds__(256)
+k_gen_slice(int Nk, int nb, int N, int64_t Np, BseModel md, const double *__restrict__ dE,
+            const z_t *__restrict__ u, const z_t *__restrict__ a, const double *__restrict__ Kt,
+            const int *__restrict__ E, uint16_t *A) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (ti < tj) return;
+    extern __shared__ z_t gsm[];
+    __shared__ z_t tile[kGT][kGT + 1];             // tile[r][c] = H(i0 + r, j0 + c)
+    __shared__ z_t ui[kGT], uj[kGT];
+    __shared__ double dEi[kGT];
+    const int R = md.rank_x;
+    z_t *sai = gsm, *saj = gsm + kGT * R;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = ti * kGT, j0 = tj * kGT;
+    const bool diag = ti == tj;
+    stage_tile(i0, j0, N, R, a, u, dE, sai, saj, ui, uj, dEi);
+    __syncthreads();
+    const int I = i0 + tx;
+    for (int c = ty; c < kGT; c += 8) {
+        const int J = j0 + c;
+        z_t h = zmk(0.0, 0.0);
+        if (!(diag && tx < c) && I < N && J < N)
+            h = bse_element(I, J, R, sai + tx, saj + c, kGT, ui[tx], uj[c], dEi[tx], Nk, nb, md.w0,
+                            Kt);
+        tile[tx][c] = h;
+    }
+    __syncthreads();
+    if (diag)                                      // the upper half of a diagonal tile
+        for (int c = ty; c < kGT; c += 8)
+            if (tx < c) tile[tx][c] = zconj(tile[c][tx]);
+    __syncthreads();
+    // direct part: row i0 + r, columns j0 + tx (consecutive K: coalesced);
+    // mirror part (off-diagonal tiles): row j0 + r, columns i0 + tx
+    for (int pass = 0; pass < (diag ? 1 : 2); pass++) {
+        const int r0 = pass == 0 ? i0 : j0, k0 = pass == 0 ? j0 : i0;
+        for (int r = ty; r < kGT; r += 8) {
+            const int64_t i = r0 + r, k = k0 + tx;
+            const z_t h = pass == 0 ? tile[r][tx] : zconj(tile[tx][r]);
+            int e = (i < N) ? E[i] : INT_MIN;
+            if (e == INT_MIN) e = 0;
+            int tr[kS], tim[kS];
+            split_digits(h.x, e, tr);
+            split_digits(h.y, e, tim);
+#pragma unroll
+            for (int p = 0; p < kS; p++) {
+                A[tiled_index(p * 2 + 0, k, i, Np, Np)] = bf16_exact(slice_value(tr[p], p));
+                A[tiled_index(p * 2 + 1, k, i, Np, Np)] = bf16_exact(slice_value(tim[p], p));
+            }
+        }
     }
 }
 
@@ -1034,6 +1159,34 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     dim3 g2((unsigned)(Np / 32), (unsigned)(Np / 32));
     k_slice_h<<<g2, dim3(32, 8), 0, st>>>(N, Np, N, Np, H, ldh, oh->E, (uint16_t *)oh->A);
     bse_count_launches(1);
+    if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * (Np / kKC)),
+                  kBM))
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const double *dE,
+                              const z_t *u, const z_t *a, const double *Kt, OzakiH *oh,
+                              ChaseScalars *sc, cudaStream_t st) {
+    const int64_t N = (int64_t)Nk * Nv * Nc;
+    const int64_t Np = ozaki_padded(N);
+    oh->N = N;
+    oh->Np = Np;
+    k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
+    bse_count_launches(1);
+    const int dyn = 2 * kGT * std::max(md.rank_x, 1) * (int)sizeof(z_t);
+    static std::once_flag once[2][kMaxDevices];
+    static cudaError_t attr[2][kMaxDevices];
+    cudaError_t ae = smem_attr_once(once[0], attr[0], (const void *)k_gen_row_exponent, 2 * kGT * 64 * (int)sizeof(z_t));
+    if (ae == cudaSuccess)
+        ae = smem_attr_once(once[1], attr[1], (const void *)k_gen_slice, 2 * kGT * 64 * (int)sizeof(z_t));
+    if (ae != cudaSuccess) return ae;
+    const unsigned T = (unsigned)((N + kGT - 1) / kGT), Tp = (unsigned)(Np / kGT);
+    k_gen_row_exponent<<<dim3(T, T), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a, Kt,
+                                                              oh->E, sc);
+    k_gen_slice<<<dim3(Tp, Tp), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, Np, md, dE, u, a, Kt,
+                                                        oh->E, (uint16_t *)oh->A);
+    bse_count_launches(2);
     if (!make_map((CUtensorMap *)oh->tmap, oh->A, (uint64_t)Np, (uint64_t)(kS * 2 * (Np / kKC)),
                   kBM))
         return cudaErrorInvalidValue;

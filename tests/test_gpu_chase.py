@@ -411,6 +411,30 @@ def test_solve_nex_tuner_matches_oracle(ctx, c1):
         ctx.solve(Hd, 50, 10, nex_damping=1.5)
 
 
+@pytest.mark.parametrize("shape,model,precision", [
+    ((125, 4, 4), None, pkg.CHASE_FP64),
+    ((7, 3, 5), None, pkg.CHASE_FP64),                     # ragged N = 105
+    ((40, 4, 4), dict(rank_x=3, w0=0.5), pkg.CHASE_MIXED_FP32),
+    ((41, 2, 3), dict(x0=0.0), pkg.CHASE_FP64),            # N = 246, no exchange
+])
+def test_solve_bse_without_stored_h_is_bitwise_the_same(ctx, shape, model, precision):
+    """chase_solve_bse generates the synthetic Hamiltonian straight into its
+    tensor-core slices; the solve is bit for bit the one on the stored H."""
+    Nk, Nv, Nc = shape
+    N = Nk * Nv * Nc
+    nev, nex = min(20, N // 4), min(10, N // 8)
+    Hd = ctx.build_hamiltonian(9, Nk, Nv, Nc, model)
+    a = ctx.solve(Hd, nev, nex, precision=precision, seed=2)
+    del Hd
+    b = ctx.solve_bse(9, Nk, Nv, Nc, nev, nex, precision=precision, model=model, seed_start=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
+    assert torch.equal(a[1], b[1])
+    assert a[3]["iters"] == b[3]["iters"] and a[3]["matvecs"] == b[3]["matvecs"]
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.solve_bse(9, Nk, Nv, Nc, nev, nex, precision=pkg.CHASE_FP64_DFMA)
+    assert ei.value.status == pkg.BSE_EINVAL
+
+
 def test_solve_is_deterministic(ctx):
     Hd = ctx.build_hamiltonian(4, 30, 4, 4)
     a = ctx.solve(Hd, 30, 15)
@@ -560,6 +584,10 @@ def test_solve_c3_certified(ctx):
     gap = lam[nev] - evals[-1]
     assert gap > 1e-6 * normH
     assert np.linalg.norm(rn) / gap <= 1e-5                    # Davis-Kahan sin(angle)
+    # the same solve without the stored H (40 GB less): bit for bit the same
+    e3, V3, r3, _ = ctx.solve_bse(0, Nk, 4, 4, nev, nex, tol=1e-10, deg_max=36, degree_group=48)
+    assert np.array_equal(e3, evals) and np.array_equal(r3, resid) and torch.equal(V3, Vd)
+    del V3
     e2, V2, r2, st2 = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36, seed=1,
                                 precision=pkg.CHASE_MIXED_FP32, degree_group=48)
     assert np.max(r2) <= 1e-10
