@@ -446,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
             "value": t_m, "unit": UNIT, "iters": st_m["iters"],
             "filter_matvecs": st_m["filter_matvecs"],
             "filter_matvecs_low": st_m["filter_matvecs_low"],
+            "filter_matvecs_mid": st_m["filter_matvecs_mid"],
             "max_resid": float(np.max(r_m)),
             "eval_rel_diff_vs_fp64": {"max": float(np.max(rel)), "median": float(np.median(rel)),
                                       "per_pair": [float("%.3g" % x) for x in rel]},

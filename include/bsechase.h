@@ -67,8 +67,9 @@ typedef enum {
     CHASE_MIXED_FP32 = 1, /* filter products at FP32-level accuracy on the
                              tensor cores (first 4 slices: 32 bits relative to
                              the row/column maximum, 10 slice pairs) while
-                             every unlocked residual exceeds 1e-6, then
-                             FP64-accurate filter sweeps; Lanczos, QR,
+                             every unlocked residual exceeds 1e-6, then on 5
+                             slices (15 pairs) while every one exceeds 1e-8,
+                             then FP64-accurate filter sweeps; Lanczos, QR,
                              Rayleigh-Ritz and residuals as in CHASE_FP64.
                              In single-phase entry points it selects the
                              FP32-level product.                             */
@@ -139,7 +140,8 @@ typedef struct {
     double alpha, beta, lower; /* final damped interval and filter lower point */
     int64_t kernel_launches;   /* CUDA kernels this solve launched            */
     int64_t filter_launches;   /* filter matrix-product launches              */
-    int64_t filter_matvecs_low; /* filter products at FP32-level accuracy     */
+    int64_t filter_matvecs_low; /* filter products at FP32-level accuracy
+                                   (4 slices; CHASE_MIXED_FP32)               */
     /* The tensor-core product kernel alone (precisions FP64 and MIXED_FP32),
      * timed with CUDA events around each launch on the solver's stream:    */
     double tc_kernel_ms;        /* summed launch durations                    */
@@ -148,6 +150,8 @@ typedef struct {
                                 /* multiply-add per slice pair) / duration    */
     int nex_used;               /* nex at the end (differs from the argument
                                    when the nex tuner grew it)                */
+    int64_t filter_matvecs_mid; /* filter products on 5 slices
+                                   (CHASE_MIXED_FP32)                         */
 } chase_stats;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
@@ -284,6 +288,13 @@ int chase_gram_noalloc(const void *d_A, int64_t lda, const void *d_B, int64_t ld
  * repeated HEMM).  d_C must not overlap d_H or d_Y. */
 int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
                int64_t ldy, int n, void *d_C, int64_t ldc, int precision);
+/* As chase_hemm on the tensor cores with the first `slices` 8-bit slices of
+ * each operand (4, 5 or 6; slice pairs p + q <= slices + 1): 6 is CHASE_FP64's
+ * product, 4 the FP32-level product of CHASE_MIXED_FP32, 5 the intermediate
+ * level that mode uses between them (about 40 bits per operand relative to
+ * its row or column maximum).  Other values: BSE_EINVAL. */
+int chase_hemm_slices(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
+                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices);
 
 /* ---- request server (continuous batching of many solves on one GPU) ------
  * The paper's BSE workflow solves sequences of related eigenproblems (k-mesh

@@ -27,6 +27,7 @@ ABI_SYMBOLS = (
     "bsechase_set_wait_limit",
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host", "chase_solve_bse",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
+    "chase_hemm_slices",
     "chase_gram", "chase_gram_noalloc",
     "chase_server_create", "chase_server_submit", "chase_server_poll", "chase_server_wait",
     "chase_server_evecs", "chase_server_release", "chase_server_info", "chase_server_destroy",
@@ -65,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("lower", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64),
                 ("tc_kernel_ms", ctypes.c_double), ("tc_kernel_launches", ctypes.c_int64),
-                ("tc_kernel_tflops", ctypes.c_double), ("nex_used", ctypes.c_int)]
+                ("tc_kernel_tflops", ctypes.c_double), ("nex_used", ctypes.c_int),
+                ("filter_matvecs_mid", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -152,6 +154,8 @@ def load():
     L.chase_rayleigh_ritz.restype = i32
     L.chase_hemm.argtypes = [P, P, i64, i64, P, i64, i32, P, i64, i32]
     L.chase_hemm.restype = i32
+    L.chase_hemm_slices.argtypes = L.chase_hemm.argtypes
+    L.chase_hemm_slices.restype = i32
     L.chase_gram.argtypes = [P, P, i64, P, i64, i64, i32, i32, P, i64]
     L.chase_gram.restype = i32
     L.chase_gram_noalloc.argtypes = [P, i64, P, i64, i64, i32, i32, P, i64, P]
@@ -407,13 +411,16 @@ class Context:
         self._check(rc)
         return V
 
-    def hemm(self, H, Y, precision=CHASE_FP64, out=None):
-        """C = H Y (the filter's product) as a new column-major tensor."""
+    def hemm(self, H, Y, precision=CHASE_FP64, out=None, slices=None):
+        """C = H Y (the filter's product) as a new column-major tensor; with
+        `slices` (4, 5 or 6) the tensor-core product on that many slices
+        (chase_hemm_slices) instead of `precision`'s."""
         N, n = Y.shape
         C = colmajor_empty(N, n, device=Y.device) if out is None else out
-        rc = load().chase_hemm(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H),
-                               ctypes.c_void_p(Y.data_ptr()), _ld(Y), n,
-                               ctypes.c_void_p(C.data_ptr()), _ld(C), precision)
+        fn, last = (load().chase_hemm, precision) if slices is None else \
+            (load().chase_hemm_slices, slices)
+        rc = fn(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), ctypes.c_void_p(Y.data_ptr()),
+                _ld(Y), n, ctypes.c_void_p(C.data_ptr()), _ld(C), last)
         self._check(rc)
         return C
 

@@ -25,9 +25,13 @@ namespace {
 constexpr int kMaxM = 512;
 constexpr double kU = 0x1.0p-53;
 constexpr double kKappaMax = 1e12;             // cap on the filter's amplification
-// Mixed precision: the FP32-level filter is used while every unlocked pair's
-// residual is above this value; FP64-accurate sweeps close the solve.
+// Mixed precision: the filter runs on the first four slices (FP32 level)
+// while every unlocked pair's residual is above kMixedSwitch, on five while
+// every one is above kMixedSwitch5, then FP64-accurate sweeps close the
+// solve.  Each level's residual floor lies about a decade below its switch
+// point (four slices: near 1e-7; five: 256 times lower).
 constexpr double kMixedSwitch = 1e-6;
+constexpr double kMixedSwitch5 = 1e-8;
 constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
 
 }  // namespace
@@ -178,7 +182,7 @@ struct Hop {
     const z_t *H;
     int64_t N, ldh;
     bool tc;         // tensor-core emulation
-    bool low = false;  // FP32-level accuracy (mixed precision filter)
+    int level = OZ_S6;   // slices of the tensor-core product (mixed precision filter)
     const BseSource *bse = nullptr;   // H not stored: its slices from the generator
 };
 
@@ -232,14 +236,14 @@ int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy
               int64_t ldc, const GemmEpi &ep) {
     if (op.tc) {
         // tensor flops: 8 real flops per complex multiply-add for each of
-        // the 21 (FP64) or 10 (FP32-level) slice pairs
-        const double pairs = op.low ? 10.0 : 21.0;
+        // the 21 (FP64), 15 or 10 (FP32-level) slice pairs
+        const double pairs = oz_pairs(op.level);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         // a batched launch holds other solvers' products: not timed per product
         if (!ctx->batcher)
             kernel_events(ctx, 8.0 * pairs * (double)op.N * (double)op.N * n, &e0, &e1);
         CK(ozaki_zgemm(ctx->oh, n, Y, ldy, C, ldc, ep, ctx->ozB.p, (int *)ctx->ozF.p, ctx->sc,
-                       op.low ? 1 : 0, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st, e0,
+                       op.level, (z_t *)ctx->ozP.p, ctx->ozP.bytes, ctx->sms, ctx->st, e0,
                        e1, ctx->batcher));
     } else
         CK(launch_zgemm_nn(op.N, n, op.N, op.H, op.ldh, Y, ldy, C, ldc, ep, ctx->st));
@@ -550,7 +554,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
     tm.mark(1);
     int64_t matvecs = (int64_t)std::min<int64_t>(o.lanczos_steps, N) * o.lanczos_vecs;
-    int64_t filter_mv = 0, filter_launches = 0, filter_mv_low = 0;
+    int64_t filter_mv = 0, filter_launches = 0, filter_mv_low = 0, filter_mv_mid = 0;
     // start block: seeded columns, the first n_v0 replaced by the warm start
     CK(launch_random_block(o.seed, 5, N, m, 0, V, N, ctx->st));
     if (o.d_V0 && o.n_v0 > 0)
@@ -601,13 +605,14 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         if (precision == CHASE_MIXED_FP32) {
             double rmin = INFINITY;
             for (int j = locked; j < m; j++) rmin = std::min(rmin, res[j]);
-            fop.low = rmin > kMixedSwitch;
+            fop.level = rmin > kMixedSwitch ? OZ_S4 : rmin > kMixedSwitch5 ? OZ_S5 : OZ_S6;
         }
         if ((rc = phase_filter(ctx, fop, Va, N, ma, hdeg.data(), s.deg, lower, c, e, &mv,
                                &filter_launches)))
             return rc;
         filter_mv += mv;
-        if (fop.low) filter_mv_low += mv;
+        if (fop.level == OZ_S4) filter_mv_low += mv;
+        if (fop.level == OZ_S5) filter_mv_mid += mv;
         tm.mark(3);
         if ((rc = phase_qr(ctx, V, N, locked, Va, N, N, ma))) return rc;
         tm.mark(4);
@@ -710,6 +715,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         stats->kernel_launches = bse_launch_count() - launches0;
         stats->filter_launches = filter_launches;
         stats->filter_matvecs_low = filter_mv_low;
+        stats->filter_matvecs_mid = filter_mv_mid;
         stats->tc_kernel_ms = ctx->k_ms;
         stats->tc_kernel_launches = ctx->k_launches;
         stats->tc_kernel_tflops = ctx->k_ms > 0 ? ctx->k_flops / (ctx->k_ms * 1e9) : 0.0;
@@ -942,7 +948,7 @@ int chase_lanczos(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, in
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
-           precision == CHASE_MIXED_FP32};
+           precision == CHASE_MIXED_FP32 ? OZ_S4 : OZ_S6};
     if ((rc = hop_prepare(ctx, op, 8))) return rc;
     if ((rc = phase_lanczos(ctx, op, m, steps, runs, seed))) return rc;
     if ((rc = sync_scalars(ctx))) return rc;
@@ -971,7 +977,7 @@ int chase_filter(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, voi
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
-           precision == CHASE_MIXED_FP32};
+           precision == CHASE_MIXED_FP32 ? OZ_S4 : OZ_S6};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
     if ((rc = phase_filter(ctx, op, (z_t *)d_V, ldv, m, h_deg, s.deg, lower, c, e, matvecs)))
         return rc;
@@ -1005,7 +1011,7 @@ int chase_rayleigh_ritz(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t l
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     precision = precision_mode(precision);
     Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
-           precision == CHASE_MIXED_FP32};
+           precision == CHASE_MIXED_FP32 ? OZ_S4 : OZ_S6};
     if ((rc = hop_prepare(ctx, op, m))) return rc;
     GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_rr(ctx, op, (const z_t *)d_Q, ldq, m, s.theta, (z_t *)d_V, (z_t *)d_HV)))
@@ -1038,22 +1044,50 @@ int chase_gram(bsechase_ctx *ctx, const void *d_A, int64_t lda, const void *d_B,
     return BSE_OK;
 }
 
-int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
-               int64_t ldy, int n, void *d_C, int64_t ldc, int precision) {
-    if (!ctx) return BSE_EINVAL;
-    if (!d_H || !d_Y || !d_C || N < 1 || ldh < N || ldy < N || ldc < N || n < 1 || n > kMaxM ||
-        !precision_valid(precision))
-        return fail(ctx, BSE_EINVAL, "bad product arguments%s");
+}  // extern "C"
+
+namespace {
+
+int hemm(bsechase_ctx *ctx, const Hop &hop, int n, const void *d_Y, int64_t ldy, void *d_C,
+         int64_t ldc) {
     DeviceGuard g(ctx->device);
     int rc;
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
-    precision = precision_mode(precision);
-    Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
-           precision == CHASE_MIXED_FP32};
+    Hop op = hop;
     if ((rc = hop_prepare(ctx, op, n))) return rc;
     GemmEpi plain{};
     if ((rc = hop_apply(ctx, op, n, (const z_t *)d_Y, ldy, (z_t *)d_C, ldc, plain))) return rc;
     return sync_scalars(ctx);
+}
+
+bool hemm_args_ok(const void *d_H, int64_t N, int64_t ldh, const void *d_Y, int64_t ldy, int n,
+                  const void *d_C, int64_t ldc) {
+    return d_H && d_Y && d_C && N >= 1 && ldh >= N && ldy >= N && ldc >= N && n >= 1 && n <= kMaxM;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const void *d_Y,
+               int64_t ldy, int n, void *d_C, int64_t ldc, int precision) {
+    if (!ctx) return BSE_EINVAL;
+    if (!hemm_args_ok(d_H, N, ldh, d_Y, ldy, n, d_C, ldc) || !precision_valid(precision))
+        return fail(ctx, BSE_EINVAL, "bad product arguments%s");
+    precision = precision_mode(precision);
+    const Hop op{(const z_t *)d_H, N, ldh, precision_uses_tc(precision),
+                 precision == CHASE_MIXED_FP32 ? OZ_S4 : OZ_S6};
+    return hemm(ctx, op, n, d_Y, ldy, d_C, ldc);
+}
+
+int chase_hemm_slices(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
+                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices) {
+    if (!ctx) return BSE_EINVAL;
+    if (!hemm_args_ok(d_H, N, ldh, d_Y, ldy, n, d_C, ldc) || slices < 4 || slices > 6)
+        return fail(ctx, BSE_EINVAL, "bad product arguments%s");
+    const Hop op{(const z_t *)d_H, N, ldh, true,
+                 slices == 4 ? OZ_S4 : slices == 5 ? OZ_S5 : OZ_S6};
+    return hemm(ctx, op, n, d_Y, ldy, d_C, ldc);
 }
 
 }  // extern "C"

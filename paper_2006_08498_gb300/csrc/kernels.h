@@ -52,6 +52,14 @@ cudaError_t launch_zgemm_cn(int64_t m1, int64_t m2, int64_t K, const z_t *A, int
 // DEV_TIMEOUT.
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 
+// Accuracy levels of the tensor-core product: the first S slices of 8 bits
+// of each operand (relative to its row or column maximum), slice pairs
+// p + q <= S + 1.  OZ_S6: FP64 accuracy (21 pairs); OZ_S4: FP32 level
+// (10 pairs, products ~3e-8 relative to ||H|| ||Y||); OZ_S5: 15 pairs, 256
+// times more accurate than OZ_S4.
+enum OzLevel { OZ_S6 = 0, OZ_S4 = 1, OZ_S5 = 2 };
+inline int oz_pairs(int level) { return level == OZ_S4 ? 10 : level == OZ_S5 ? 15 : 21; }
+
 struct OzakiH {
     int64_t N = 0, Np = 0;
     void *A = nullptr;
@@ -105,8 +113,7 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
                             cudaStream_t st);
 // C[N x n] = epi(H Y), Y: N x n (ld ldy); bslices >= ozaki_b_bytes(N, n),
 // F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
-// low = 0: FP64 accuracy (6 slices, 21 slice pairs); low = 1: FP32-level
-// accuracy (the first four slices, 10 pairs, all exact).
+// level (OzLevel): how many slices of each operand take part.
 // K is split across CTAs (raw int64 + FP32 partials in `partials`, summed in a fixed
 // order) when that fills the `sms` multiprocessors better.  When ev0/ev1
 // are given they are recorded on `st` just before and after the
@@ -115,7 +122,7 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
 // with other threads' products (ev0/ev1 are then not recorded).
 struct OzBatcher;
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
-                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
+                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int level,
                         z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
                         cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
                         OzBatcher *batcher = nullptr);

@@ -79,8 +79,9 @@ constexpr int kHalf = kN / 2;                         // columns per drain threa
 
 // Variants: slices 1..NSL of each operand, pairs with p + q <= NSL + 1;
 // diagonals 2..EXT exact, diagonals EXT+1..NSL+1 (if any) in the FP32 tail.
-// FP64 accuracy: (6, 5).  Mixed precision: (4, 5): 32 bits per operand
-// relative to its row/column maximum, every diagonal exact.
+// FP64 accuracy: (6, 5).  The mixed precision mode's cheaper levels: (4, 5),
+// 32 bits per operand relative to its row/column maximum, every diagonal
+// exact; (5, 5), 40 bits, diagonal 6 in the tail.
 template <int NSL, int EXT>
 struct OzCfg {
     static constexpr int kSl = NSL;
@@ -91,8 +92,10 @@ struct OzCfg {
 };
 using CfgFP64 = OzCfg<6, 5>;
 using CfgMixed = OzCfg<4, 5>;
+using CfgMid = OzCfg<5, 5>;
 static_assert(CfgFP64::kSmem <= 232448 && CfgFP64::kAcc * kN <= kTmemCols, "resources");
 static_assert(CfgMixed::kSmem <= 232448 && CfgMixed::kAcc * kN <= kTmemCols, "resources");
+static_assert(CfgMid::kSmem <= 232448 && CfgMid::kAcc * kN <= kTmemCols, "resources");
 static_assert(kN % 16 == 0 && kW % 8 == 0 && kHalf % 16 == 0, "MMA N, TMA box rows, TMEM loads");
 static_assert(kBPart % 1024 == 0 && kATile % 1024 == 0, "128-byte swizzle atoms stay 1024-aligned");
 
@@ -585,8 +588,8 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
     constexpr int S = Cfg::kSl;
     constexpr int S2 = 2 * S;
     constexpr int kEx = Cfg::kEx;              // diagonals 2..kEx exact
-    static_assert(kEx == 5 && S >= 4 && S % 2 == 0,
-                  "FirstPassOrder, its slice pairs and the barrier groups assume kEx = 5, even S >= 4");
+    static_assert(kEx == 5 && S >= 4 && S <= 6,
+                  "FirstPassOrder and the barrier groups assume kEx = 5 and 4 <= S <= 6");
     constexpr int kNEx = kEx - 1;              // exact accumulators
     constexpr bool kTail = Cfg::kTail;
     constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
@@ -795,10 +798,21 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                             // the chunk's first pass in FirstPassOrder, two slices at a
                             // time, so the operands released last in the previous
                             // chunk are needed last; the two MMAs of one K step share
-                            // A through the collector buffer
+                            // A through the collector buffer (an odd S ends with
+                            // one slice, A read from shared memory)
 #pragma unroll
                             for (int t = 0; t < S; t += 2) {
-                                const int qa = kFirst.q[t], qb = kFirst.q[t + 1];
+                                const int qa = kFirst.q[t];
+                                if (t + 1 == S) {
+                                    if (!step(0, qa, 0)) {
+                                        ok = false;
+                                        break;
+                                    }
+#pragma unroll
+                                    for (int kk = 1; kk < kKC / 16; kk++) step(kk, qa, 0);
+                                    continue;
+                                }
+                                const int qb = kFirst.q[t + 1 < S ? t + 1 : 0];
                                 if (!step(0, qa, tc::A_FILL) || !step(0, qb, tc::A_LASTUSE)) {
                                     ok = false;   // fails only in a wait
                                     break;
@@ -1209,8 +1223,12 @@ cudaError_t launch_variant(const OzBatch &b, int sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const OzBatch &b, int low, int sms, cudaStream_t st) {
-    return low ? launch_variant<CfgMixed>(b, sms, st) : launch_variant<CfgFP64>(b, sms, st);
+cudaError_t launch_batch(const OzBatch &b, int level, int sms, cudaStream_t st) {
+    switch (level) {
+    case OZ_S4: return launch_variant<CfgMixed>(b, sms, st);
+    case OZ_S5: return launch_variant<CfgMid>(b, sms, st);
+    default: return launch_variant<CfgFP64>(b, sms, st);
+    }
 }
 
 // A batch of one product.
@@ -1245,7 +1263,7 @@ struct OzBatcher {
     std::condition_variable cv;
     struct Pending {
         OzJob job;
-        int low = 0;
+        int level = OZ_S6;
         cudaEvent_t ready = nullptr, done = nullptr;
         bool launched = false;
         cudaError_t err = cudaSuccess;
@@ -1315,12 +1333,12 @@ cudaEvent_t ready_event() {
     return ev;
 }
 
-// Run job (with its precision) through the batcher; returns after `st` waits
-// for the launch that contains it.
-cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int low, cudaStream_t st) {
+// Run job (with its accuracy level) through the batcher; returns after `st`
+// waits for the launch that contains it.
+cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int level, cudaStream_t st) {
     OzBatcher::Pending me;
     me.job = job;
-    me.low = low;
+    me.level = level;
     me.ready = ready_event();
     if (!me.ready) return cudaErrorUnknown;
     cudaError_t e = cudaEventRecord(me.ready, st);
@@ -1342,9 +1360,9 @@ cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int low, cudaStream_t st) {
                b->cv.wait_until(lk, t_end) != std::cv_status::timeout) {
         }
         std::vector<OzBatcher::Pending *> take;
-        const int low0 = b->queue.front()->low;
+        const int level0 = b->queue.front()->level;
         for (auto it = b->queue.begin(); it != b->queue.end() && (int)take.size() < kMaxJobs;) {
-            if ((*it)->low == low0) {
+            if ((*it)->level == level0) {
                 take.push_back(*it);
                 it = b->queue.erase(it);
             } else {
@@ -1374,7 +1392,7 @@ cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int low, cudaStream_t st) {
         }
         for (size_t k = 0; k < take.size() && le == cudaSuccess; k++)
             le = cudaStreamWaitEvent(b->st, take[k]->ready, 0);
-        if (le == cudaSuccess) le = launch_batch(bt, low0, b->sms, b->st);
+        if (le == cudaSuccess) le = launch_batch(bt, level0, b->sms, b->st);
         if (le == cudaSuccess) le = cudaEventRecord(done, b->st);
         lk.lock();
         for (auto *p : take) {
@@ -1409,7 +1427,7 @@ cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int low, cudaStream_t st) {
 }  // namespace
 
 cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t *C, int64_t ldc,
-                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int low,
+                        const GemmEpi &ep, void *bslices, int *F, ChaseScalars *sc, int level,
                         z_t *partials, size_t partial_bytes, int sms, cudaStream_t st,
                         cudaEvent_t ev0, cudaEvent_t ev1, OzBatcher *batcher) {
     if (n <= 0) return cudaSuccess;
@@ -1448,10 +1466,10 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     const OzBatch one = single(tmA, tmB, a);
     cudaError_t e;
     if (batcher) {
-        e = ozb_run(batcher, one.job[0], low, st);   // launched with other solvers' products
+        e = ozb_run(batcher, one.job[0], level, st);   // launched with other solvers' products
     } else {
         if (ev0) cudaEventRecord(ev0, st);
-        e = launch_batch(one, low, sms, st);
+        e = launch_batch(one, level, sms, st);
         if (ev1) cudaEventRecord(ev1, st);
     }
     if (e != cudaSuccess) return e;
@@ -1526,7 +1544,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
-    cudaError_t e = launch_batch(single(tmA, tmB, a), 0, sms, st);
+    cudaError_t e = launch_batch(single(tmA, tmB, a), OZ_S6, sms, st);
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((M + 255) / 256), (unsigned)n);
     k_gen_reduce<<<gr, 256, 0, st>>>(M, n, nsplit, a.P, a.E, a.F, mode, D, ldd, shift, hermitize, C, ldc);

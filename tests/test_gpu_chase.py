@@ -139,6 +139,26 @@ def test_hemm_fp32_level(ctx):
     assert np.max(err) >= 1e-13          # it is not the FP64-accurate product
 
 
+def test_hemm_slice_levels(ctx):
+    """The product on 4, 5 and 6 slices (chase_hemm_slices): each slice adds
+    8 bits per operand, so each level's error is about 256 times below the
+    previous one's (at least 30 times here); 6 and 4 slices are bit for bit
+    the products of CHASE_FP64 and CHASE_MIXED_FP32."""
+    A, _ = hermitian(700, 5)
+    Y = block(700, 50, 6)
+    Ad, Yd = dev(A), dev(Y)
+    C = {s: ctx.hemm(Ad, Yd, slices=s) for s in (4, 5, 6)}
+    err = {s: np.max(colwise_err(host(C[s]), A, Y)) for s in C}
+    assert err[4] <= 1e-8 and err[5] <= 1e-10 and err[6] <= EMUL_TOL
+    assert err[4] >= 30 * err[5] and err[5] >= 30 * err[6]
+    assert torch.equal(C[6], ctx.hemm(Ad, Yd, precision=pkg.CHASE_FP64))
+    assert torch.equal(C[4], ctx.hemm(Ad, Yd, precision=pkg.CHASE_MIXED_FP32))
+    for bad in (3, 7):
+        with pytest.raises(pkg.BseError) as ei:
+            ctx.hemm(Ad, Yd, slices=bad)
+        assert ei.value.status == pkg.BSE_EINVAL
+
+
 def test_hemm_zero_column_and_bse_matrix(ctx):
     H = oracle.build_h(0, 125, 4, 4)
     Y = block(2000, 75, 9)
@@ -375,6 +395,7 @@ def test_solve_mixed_precision(ctx, c1):
     _check_solution(H, evals, V, resid, 50, w_exact=w, ref=ref["evecs"])
     assert np.max(resid) <= 1e-10
     assert 0 < st["filter_matvecs_low"] < st["filter_matvecs"]
+    assert st["filter_matvecs_low"] + st["filter_matvecs_mid"] < st["filter_matvecs"]
     # both solves take their Ritz values from tensor-core products with
     # 48-bit slices (relative to row / column maxima, |H| ~ 14 here), so they
     # agree to a few 1e-12; both are within 1e-10 of the exact eigenvalues
