@@ -152,6 +152,10 @@ typedef struct {
                                    when the nex tuner grew it)                */
     int64_t filter_matvecs_mid; /* filter products on 5 slices
                                    (CHASE_MIXED_FP32)                         */
+    int64_t h2d_bytes, d2h_bytes; /* host<->device bytes copied by
+                                   chase_solve_host (0 for the other calls)   */
+    double ms_h2d;              /* chase_solve_host: copy of H's lower
+                                   triangle and its mirroring on the device   */
 } chase_stats;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
@@ -172,6 +176,15 @@ const char *bsechase_last_error(const bsechase_ctx *ctx);
  * stays usable.  A short limit makes that path run on purpose (failure
  * detection tests).  The paper has no counterpart.  Errors: BSE_EINVAL. */
 int bsechase_set_wait_limit(bsechase_ctx *ctx, double seconds);
+
+/* Page-locked host memory for the host-buffer calls (chase_solve_host):
+ * *p receives `bytes` of host memory allocated by the CUDA runtime, which the
+ * copy engines read at the host link's full rate for as long as it lives.
+ * Free it with bsechase_host_free.  Errors: BSE_EINVAL (p NULL or bytes 0),
+ * BSE_ENOMEM. */
+int bsechase_host_alloc(void **p, size_t bytes);
+/* Free memory from bsechase_host_alloc (NULL is ignored).  Errors: BSE_ECUDA. */
+int bsechase_host_free(void *p);
 
 /* Dimension N = Nk * Nv * Nc of the BSE Hamiltonian (Sec. 2: the pair index
  * runs over valence bands, conduction bands and k-points); -1 if invalid. */
@@ -218,10 +231,13 @@ int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
                     int precision, const chase_opts *opts, double *h_evals, void *d_evecs,
                     int64_t ldz, double *h_resid, chase_stats *stats);
 
-/* As chase_solve with every matrix in HOST memory: h_H (N x N) is copied to
- * a context-owned device buffer and the eigenvectors are copied back into
- * h_evecs (N x nev, ld = ldz).  Host buffers should be pinned for full
- * transfer speed.  Same errors as chase_solve. */
+/* As chase_solve with every matrix in HOST memory: the lower triangle of h_H
+ * (N x N, diagonal included) is copied to a context-owned device buffer, the
+ * upper triangle is taken as its conjugate transpose (H is Hermitian; the
+ * paper's reader likewise holds one triangle, Sec. 3), and the eigenvectors
+ * are copied back into h_evecs (N x nev, ld = ldz).  The strict upper triangle
+ * of h_H is never read.  Host buffers should be pinned for full transfer
+ * speed.  Same errors as chase_solve. */
 int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh, int nev,
                      int nex, double tol, int deg_max, int precision, const chase_opts *opts,
                      double *h_evals, void *h_evecs, int64_t ldz, double *h_resid,

@@ -24,7 +24,7 @@ CHASE_FP64, CHASE_MIXED_FP32, CHASE_MIXED_BF16X3, CHASE_FP64_DFMA = 0, 1, 2, 3
 # Every symbol include/bsechase.h declares.
 ABI_SYMBOLS = (
     "bsechase_create", "bsechase_destroy", "bsechase_strerror", "bsechase_last_error",
-    "bsechase_set_wait_limit",
+    "bsechase_set_wait_limit", "bsechase_host_alloc", "bsechase_host_free",
     "bse_dim", "bse_build_hamiltonian", "chase_solve", "chase_solve_host", "chase_solve_bse",
     "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_hemm",
     "chase_hemm_slices",
@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("filter_launches", ctypes.c_int64), ("filter_matvecs_low", ctypes.c_int64),
                 ("tc_kernel_ms", ctypes.c_double), ("tc_kernel_launches", ctypes.c_int64),
                 ("tc_kernel_tflops", ctypes.c_double), ("nex_used", ctypes.c_int),
-                ("filter_matvecs_mid", ctypes.c_int64)]
+                ("filter_matvecs_mid", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("ms_h2d", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -131,6 +132,10 @@ def load():
     L.bsechase_last_error.restype = ctypes.c_char_p
     L.bsechase_set_wait_limit.argtypes = [P, dbl]
     L.bsechase_set_wait_limit.restype = i32
+    L.bsechase_host_alloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]
+    L.bsechase_host_alloc.restype = i32
+    L.bsechase_host_free.argtypes = [P]
+    L.bsechase_host_free.restype = i32
     L.bse_dim.argtypes = [i32, i32, i32]
     L.bse_dim.restype = i64
     L.bse_build_hamiltonian.argtypes = [P, u64, i32, i32, i32, ctypes.POINTER(Model), P, i64]
@@ -225,6 +230,22 @@ def gram_noalloc(A, B, out, stream=None):
                                          ctypes.c_void_p(B.data_ptr()), _ld(B), K, m1, m2,
                                          ctypes.c_void_p(out.data_ptr()), _ld(out),
                                          ctypes.c_void_p(stream.cuda_stream))
+
+
+def host_empty(shape, dtype=np.complex128, order="F"):
+    """Uninitialised numpy array in page-locked host memory from
+    bsechase_host_alloc (freed when the array and its views are gone): the
+    host buffers of solve_host copy at the host link's full rate."""
+    import weakref
+    dtype = np.dtype(dtype)
+    nbytes = int(np.prod(shape)) * dtype.itemsize
+    p = ctypes.c_void_p()
+    rc = load().bsechase_host_alloc(ctypes.byref(p), max(nbytes, 1))
+    if rc != BSE_OK:
+        raise BseError(rc, "host allocation of %d bytes" % nbytes)
+    buf = (ctypes.c_char * max(nbytes, 1)).from_address(p.value)
+    weakref.finalize(buf, load().bsechase_host_free, p.value)
+    return np.frombuffer(buf, dtype=dtype, count=int(np.prod(shape))).reshape(shape, order=order)
 
 
 def colmajor_empty(rows, cols, device="cuda", dtype=None):

@@ -33,6 +33,7 @@ constexpr double kKappaMax = 1e12;             // cap on the filter's amplificat
 constexpr double kMixedSwitch = 1e-6;
 constexpr double kMixedSwitch5 = 1e-8;
 constexpr int64_t kCnWork = (int64_t)1 << 20;   // split-K partials (complex elements)
+constexpr int64_t kHostCopyCols = 256;           // columns per copy of the lower triangle
 
 }  // namespace
 
@@ -801,6 +802,22 @@ int bsechase_set_wait_limit(bsechase_ctx *ctx, double seconds) {
     return BSE_OK;
 }
 
+int bsechase_host_alloc(void **p, size_t bytes) {
+    if (!p || bytes == 0) return BSE_EINVAL;
+    *p = nullptr;
+    if (cudaHostAlloc(p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return BSE_ENOMEM;
+    }
+    return BSE_OK;
+}
+
+int bsechase_host_free(void *p) {
+    if (!p) return BSE_OK;
+    return cudaFreeHost(p) == cudaSuccess ? BSE_OK : BSE_ECUDA;
+}
+
 int bsechase_create(bsechase_ctx **out, int device, void *stream) {
     if (!out) return BSE_EINVAL;
     *out = nullptr;
@@ -829,7 +846,7 @@ int bsechase_create(bsechase_ctx **out, int device, void *stream) {
     if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         ctx->sms = 152;
     ctx->ev_ok = true;
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < kCtxEvents; i++)
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) ctx->ev_ok = false;
     *out = ctx;
     return BSE_OK;
@@ -845,7 +862,7 @@ void bsechase_destroy(bsechase_ctx *ctx) {
     }
     if (ctx->sc) cudaFree(ctx->sc);
     if (ctx->hsc) cudaFreeHost(ctx->hsc);
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < kCtxEvents; i++)
         if (ctx->ev_ok) cudaEventDestroy(ctx->ev[i]);
     for (cudaEvent_t e : ctx->kev) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->st);
@@ -924,8 +941,22 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
     ctx->err.clear();
     if ((rc = ensure(ctx, ctx->Hdev, (size_t)N * N * sizeof(z_t)))) return rc;
     if ((rc = ensure(ctx, ctx->Zdev, (size_t)N * nev * sizeof(z_t)))) return rc;
-    CK(cudaMemcpy2DAsync(ctx->Hdev.p, N * sizeof(z_t), h_H, ldh * sizeof(z_t), N * sizeof(z_t), N,
-                         cudaMemcpyHostToDevice, ctx->st));
+    // Only the lower triangle crosses the host link (half the bytes of H; the
+    // link, not HBM, bounds this copy): rows j0.. of each block of columns
+    // j0.., then the upper triangle is mirrored on the device.
+    z_t *Hd = (z_t *)ctx->Hdev.p;
+    const z_t *Hh = (const z_t *)h_H;
+    int64_t h2d = 0;
+    if (ctx->ev_ok) cudaEventRecord(ctx->ev[8], ctx->st);
+    for (int64_t j0 = 0; j0 < N; j0 += kHostCopyCols) {
+        const int64_t w = std::min<int64_t>(kHostCopyCols, N - j0);
+        CK(cudaMemcpy2DAsync(Hd + j0 + j0 * N, N * sizeof(z_t), Hh + j0 + j0 * ldh,
+                             ldh * sizeof(z_t), (N - j0) * sizeof(z_t), w,
+                             cudaMemcpyHostToDevice, ctx->st));
+        h2d += (N - j0) * w * (int64_t)sizeof(z_t);
+    }
+    CK(launch_mirror_lower(N, Hd, N, ctx->st));
+    if (ctx->ev_ok) cudaEventRecord(ctx->ev[9], ctx->st);
     rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max,
                       precision_mode(precision), opts,
                       h_evals, (z_t *)ctx->Zdev.p, N, h_resid, stats);
@@ -933,6 +964,13 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
     CK(cudaMemcpy2DAsync(h_evecs, ldz * sizeof(z_t), ctx->Zdev.p, N * sizeof(z_t), N * sizeof(z_t),
                          nev, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    if (stats) {
+        stats->h2d_bytes = h2d;
+        stats->d2h_bytes = N * nev * (int64_t)sizeof(z_t);
+        float ms = 0.f;
+        if (ctx->ev_ok && cudaEventElapsedTime(&ms, ctx->ev[8], ctx->ev[9]) == cudaSuccess)
+            stats->ms_h2d = ms;
+    }
     return rc;
 }
 

@@ -16,6 +16,8 @@ struct DevBuf {
 
 struct BseServer;
 
+constexpr int kCtxEvents = 10;
+
 struct bsechase_ctx {
     int device = 0;
     cudaStream_t st = nullptr;
@@ -34,7 +36,7 @@ struct bsechase_ctx {
     OzakiH oh;
     int64_t wsN = 0;
     int wsM = 0;
-    cudaEvent_t ev[8];
+    cudaEvent_t ev[kCtxEvents];   // 0..6: solve phases; 8, 9: host copies
     bool ev_ok = false;
     // CUDA-event timing of every tensor-core product launch: event pairs
     // recorded on st, read back at the solver's synchronisation points

@@ -148,6 +148,9 @@ cudaError_t launch_residuals(int64_t N, int nc, const z_t *HV, int64_t ldhv, con
                              int64_t ldv, const double *theta, double *r, double *work,
                              ChaseScalars *sc, cudaStream_t st);
 // out[:, j] = in[:, perm ? perm[j] : j]
+// H(i, j) = conj(H(j, i)) for i < j (N x N, column-major): the Hermitian
+// matrix whose lower triangle H holds.
+cudaError_t launch_mirror_lower(int64_t N, z_t *H, int64_t ldh, cudaStream_t st);
 cudaError_t launch_copy_cols(int64_t N, int nc, const z_t *in, int64_t ldin, z_t *out,
                              int64_t ldout, const int *perm, cudaStream_t st);
 // Seeded complex block (2u-1) + i(2u'-1) from SplitMix64, as in the generator

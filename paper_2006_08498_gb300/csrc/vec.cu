@@ -212,6 +212,36 @@ cudaError_t launch_residuals(int64_t N, int nc, const z_t *HV, int64_t ldhv, con
     return cudaGetLastError();
 }
 
+// The strict upper triangle from the lower one: H(i, j) = conj(H(j, i)) for
+// i < j.  One 32 x 32 tile of the upper triangle per CTA (row tile ti <=
+// column tile tj), read from its mirror tile and written through shared
+// memory, so loads and stores are both coalesced.  A diagonal tile reads all
+// of itself before it writes its upper half.
+__global__ void __launch_bounds__(256) k_mirror_lower(int64_t N, z_t *H, int64_t ldh) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (ti > tj) return;
+    __shared__ z_t t[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t i0 = (int64_t)ti * 32, j0 = (int64_t)tj * 32;
+    for (int c = ty; c < 32; c += 8) {               // t[c][x] = H(j0 + x, i0 + c)
+        const int64_t r = j0 + tx, col = i0 + c;
+        if (r < N && col < N) t[c][tx] = H[r + col * ldh];
+    }
+    __syncthreads();
+    for (int c = ty; c < 32; c += 8) {               // H(i0 + x, j0 + c) = conj(t[x][c])
+        const int64_t r = i0 + tx, col = j0 + c;
+        if (r < N && col < N && r < col) H[r + col * ldh] = zconj(t[tx][c]);
+    }
+}
+
+cudaError_t launch_mirror_lower(int64_t N, z_t *H, int64_t ldh, cudaStream_t st) {
+    if (N <= 1) return cudaSuccess;
+    const unsigned T = (unsigned)((N + 31) / 32);
+    k_mirror_lower<<<dim3(T, T), dim3(32, 8), 0, st>>>(N, H, ldh);
+    bse_count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_cols(int64_t N, int nc, const z_t *in, int64_t ldin, z_t *out,
                              int64_t ldout, const int *perm, cudaStream_t st) {
     if (nc <= 0 || N <= 0) return cudaSuccess;

@@ -490,6 +490,27 @@ def test_solve_host_buffers_equal_device(ctx):
     assert np.array_equal(host(V1), V2)
 
 
+def test_solve_host_reads_only_the_lower_triangle(ctx):
+    """chase_solve_host copies the lower triangle and mirrors it: garbage
+    (NaN) in the strict upper triangle is never read, and the result is bit
+    for bit the device solve of the Hermitian matrix, at a ragged N that spans
+    several copy blocks and mirror tiles.  The host buffers come from
+    bsechase_host_alloc (pkg.host_empty)."""
+    H = oracle.build_h(3, 23, 4, 7)                 # N = 644
+    N = H.shape[0]
+    Hg = pkg.host_empty((N, N))
+    Hg[:] = H
+    Hg[np.triu_indices(N, 1)] = np.nan
+    Zg = pkg.host_empty((N, 30))
+    e1, V1, r1, _ = ctx.solve(dev(H), 30, 15)
+    e2, V2, r2, st = ctx.solve_host(Hg, 30, 15, evecs=Zg)
+    assert V2 is Zg
+    assert np.array_equal(e1, e2) and np.array_equal(r1, r2)
+    assert np.array_equal(host(V1), V2)
+    assert st["h2d_bytes"] == 16 * sum((N - j) * min(256, N - j) for j in range(0, N, 256))
+    assert st["d2h_bytes"] == 16 * N * 30 and st["ms_h2d"] > 0
+
+
 def test_warm_start_fewer_iterations(ctx):
     Hd = ctx.build_hamiltonian(0, 40, 4, 4)
     e1, V1, _, s1 = ctx.solve(Hd, 40, 20)
