@@ -126,6 +126,16 @@ typedef struct {
                             nex_damping, nex grows once to min(max(2 nex,
                             nex + 8), min(N, 512) - nev).  The new columns are
                             the seeded start block's next columns. */
+    int half_storage;    /* 0 (default): the tensor-core slices of all of H
+                            (24 N^2 bytes).  1: of its lower triangle only
+                            (12 N^2 bytes), the strict upper triangle never
+                            read (H is Hermitian; the paper's reader holds one
+                            triangle, Sec. 3): rows are scaled symmetrically,
+                            H = T S T with t_i = sqrt(max_k |H_ik|), so that
+                            one exponent serves S's rows and its columns, and
+                            the product reads each stored tile of S both
+                            ways.  Tensor-core precisions and chase_solve /
+                            chase_solve_host only (BSE_EINVAL otherwise). */
 } chase_opts;
 
 /* Per-solve statistics (times in milliseconds, CUDA events on the stream). */
@@ -308,9 +318,12 @@ int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const
  * each operand (4, 5 or 6; slice pairs p + q <= slices + 1): 6 is CHASE_FP64's
  * product, 4 the FP32-level product of CHASE_MIXED_FP32, 5 the intermediate
  * level that mode uses between them (about 40 bits per operand relative to
- * its row or column maximum).  Other values: BSE_EINVAL. */
+ * its row or column maximum).  half_storage = 1: the product on the slices
+ * of H's lower triangle (chase_opts.half_storage; the strict upper triangle
+ * of d_H is not read).  Other values: BSE_EINVAL. */
 int chase_hemm_slices(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
-                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices);
+                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices,
+                      int half_storage);
 
 /* ---- request server (continuous batching of many solves on one GPU) ------
  * The paper's BSE workflow solves sequences of related eigenproblems (k-mesh

@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("lanczos_steps", ctypes.c_int), ("lanczos_vecs", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("d_V0", ctypes.c_void_p),
                 ("ldv0", ctypes.c_int64), ("n_v0", ctypes.c_int),
-                ("degree_group", ctypes.c_int), ("nex_damping", ctypes.c_double)]
+                ("degree_group", ctypes.c_int), ("nex_damping", ctypes.c_double),
+                ("half_storage", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -159,7 +160,7 @@ def load():
     L.chase_rayleigh_ritz.restype = i32
     L.chase_hemm.argtypes = [P, P, i64, i64, P, i64, i32, P, i64, i32]
     L.chase_hemm.restype = i32
-    L.chase_hemm_slices.argtypes = L.chase_hemm.argtypes
+    L.chase_hemm_slices.argtypes = L.chase_hemm.argtypes + [i32]
     L.chase_hemm_slices.restype = i32
     L.chase_gram.argtypes = [P, P, i64, P, i64, i64, i32, i32, P, i64]
     L.chase_gram.restype = i32
@@ -321,9 +322,9 @@ class Context:
     # -------------------------------------------------------------- solve
     @staticmethod
     def _opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group=0,
-              nex_damping=0.0):
+              nex_damping=0.0, half_storage=False):
         o = Opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, 0, 0, degree_group,
-                 nex_damping)
+                 nex_damping, int(half_storage))
         if V0 is not None:
             o.d_V0 = ctypes.c_void_p(V0.data_ptr())
             o.ldv0 = _ld(V0)
@@ -332,9 +333,12 @@ class Context:
 
     def solve(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64, deg_init=20,
               max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0, V0=None,
-              evecs=None, allow_noconv=False, degree_group=0, nex_damping=0.0):
+              evecs=None, allow_noconv=False, degree_group=0, nex_damping=0.0,
+              half_storage=False):
         """Lowest nev eigenpairs of the device Hermitian H (column-major).
-        Returns (evals ndarray, evecs tensor N x nev, resid ndarray, stats)."""
+        Returns (evals ndarray, evecs tensor N x nev, resid ndarray, stats).
+        half_storage: the tensor-core slices of H's lower triangle only
+        (chase_opts.half_storage)."""
         N = H.shape[0]
         evals = np.zeros(nev)
         resid = np.zeros(nev)
@@ -342,7 +346,7 @@ class Context:
             evecs = colmajor_empty(N, nev, device=H.device)
         st = Stats()
         o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, V0, degree_group,
-                       nex_damping)
+                       nex_damping, half_storage)
         rc = load().chase_solve(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), nev, nex,
                                 tol, deg_max, precision, ctypes.byref(o), _dp(evals),
                                 ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),
@@ -384,16 +388,17 @@ class Context:
 
     def solve_host(self, H, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
                    deg_init=20, max_iter=50, lanczos_steps=25, lanczos_vecs=4, seed=0,
-                   evecs=None, degree_group=0):
+                   evecs=None, degree_group=0, half_storage=False):
         """As solve(), with H and the eigenvectors in host memory (Fortran-
-        ordered complex128 numpy arrays, ideally pinned)."""
+        ordered complex128 numpy arrays, ideally page-locked: host_empty)."""
         N = H.shape[0]
         evals = np.zeros(nev)
         resid = np.zeros(nev)
         if evecs is None:
             evecs = np.zeros((N, nev), dtype=np.complex128, order="F")
         st = Stats()
-        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, degree_group)
+        o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed, None, degree_group,
+                       0.0, half_storage)
         hp = H.data_ptr() if hasattr(H, "data_ptr") else H.ctypes.data
         ep = evecs.data_ptr() if hasattr(evecs, "data_ptr") else evecs.ctypes.data
         rc = load().chase_solve_host(self._h, ctypes.c_void_p(hp), N, _ld(H), nev, nex, tol,
@@ -432,16 +437,19 @@ class Context:
         self._check(rc)
         return V
 
-    def hemm(self, H, Y, precision=CHASE_FP64, out=None, slices=None):
+    def hemm(self, H, Y, precision=CHASE_FP64, out=None, slices=None, half_storage=False):
         """C = H Y (the filter's product) as a new column-major tensor; with
-        `slices` (4, 5 or 6) the tensor-core product on that many slices
+        `slices` (4, 5 or 6) or half_storage, the tensor-core product on that
+        many slices (default 6) of all of H or of its lower triangle
         (chase_hemm_slices) instead of `precision`'s."""
         N, n = Y.shape
         C = colmajor_empty(N, n, device=Y.device) if out is None else out
-        fn, last = (load().chase_hemm, precision) if slices is None else \
-            (load().chase_hemm_slices, slices)
+        if slices is None and not half_storage:
+            fn, last = load().chase_hemm, (precision,)
+        else:
+            fn, last = load().chase_hemm_slices, (6 if slices is None else slices, int(half_storage))
         rc = fn(self._h, ctypes.c_void_p(H.data_ptr()), N, _ld(H), ctypes.c_void_p(Y.data_ptr()),
-                _ld(Y), n, ctypes.c_void_p(C.data_ptr()), _ld(C), last)
+                _ld(Y), n, ctypes.c_void_p(C.data_ptr()), _ld(C), *last)
         self._check(rc)
         return C
 

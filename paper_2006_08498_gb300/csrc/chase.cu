@@ -72,7 +72,7 @@ void release_workspace(bsechase_ctx *ctx) {
     DevBuf *bufs[] = {&ctx->V,  &ctx->B1,      &ctx->B2,   &ctx->B3,  &ctx->G,      &ctx->R,
                       &ctx->Ri, &ctx->Yr,      &ctx->heev, &ctx->small_d, &ctx->ints, &ctx->part,
                       &ctx->lz, &ctx->tables, &ctx->Hdev, &ctx->Zdev, &ctx->ozA, &ctx->ozE,
-                      &ctx->ozB, &ctx->ozF, &ctx->ozP, &ctx->ozGA, &ctx->ozGE};
+                      &ctx->ozB, &ctx->ozF, &ctx->ozP, &ctx->ozGA, &ctx->ozGE, &ctx->ozT};
     for (DevBuf *b : bufs) {
         if (b->p) cudaFreeAsync(b->p, ctx->st);
         b->p = nullptr;
@@ -185,13 +185,16 @@ struct Hop {
     bool tc;         // tensor-core emulation
     int level = OZ_S6;   // slices of the tensor-core product (mixed precision filter)
     const BseSource *bse = nullptr;   // H not stored: its slices from the generator
+    bool tri = false;    // half storage of the slices (lower triangle of H only)
 };
 
 int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     if (!op.tc) return BSE_OK;
     int rc;
     const int64_t Np = ozaki_padded(op.N);
-    if ((rc = ensure(ctx, ctx->ozA, ozaki_a_bytes(op.N)))) return rc;
+    if ((rc = ensure(ctx, ctx->ozA, op.tri ? ozaki_a_bytes_tri(op.N) : ozaki_a_bytes(op.N))))
+        return rc;
+    if (op.tri && (rc = ensure(ctx, ctx->ozT, (size_t)2 * Np * sizeof(double)))) return rc;
     if ((rc = ensure(ctx, ctx->ozE, (size_t)Np * sizeof(int)))) return rc;
     const int mc = std::max(max_cols, 32);
     if ((rc = ensure(ctx, ctx->ozB, ozaki_b_bytes(op.N, mc)))) return rc;
@@ -205,7 +208,11 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     ctx->oh.A = ctx->ozA.p;
     ctx->oh.E = (int *)ctx->ozE.p;
     ctx->oh.wait_ns = ctx->wait_ns;
-    if (op.bse)
+    ctx->oh.t = (double *)ctx->ozT.p;
+    ctx->oh.s = ctx->oh.t ? ctx->oh.t + Np : nullptr;
+    if (op.tri && !op.bse)
+        CK(ozaki_prepare_h_tri(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
+    else if (op.bse)
         CK(ozaki_prepare_bse(op.bse->Nk, op.bse->Nv, op.bse->Nc, op.bse->md, op.bse->dE, op.bse->u,
                              op.bse->a, op.bse->Kt, &ctx->oh, ctx->sc, ctx->st));
     else
@@ -529,11 +536,15 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
         o.n_v0 = opts->n_v0;
         o.degree_group = opts->degree_group;
         o.nex_damping = opts->nex_damping;
+        o.half_storage = opts->half_storage;
     }
     if (o.d_V0 && (o.n_v0 < 0 || o.ldv0 < N)) return fail(ctx, BSE_EINVAL, "bad warm-start block%s");
     if (o.degree_group < 0) return fail(ctx, BSE_EINVAL, "degree_group must be >= 0%s");
     if (!(o.nex_damping >= 0.0 && o.nex_damping < 1.0))
         return fail(ctx, BSE_EINVAL, "nex_damping must be in [0, 1)%s");
+    if (o.half_storage != 0 && (o.half_storage != 1 || !precision_uses_tc(precision) || bse))
+        return fail(ctx, BSE_EINVAL,
+                    "half_storage = 1 needs a tensor-core precision and a stored H%s");
     const bool tuner = o.nex_damping > 0.0;
     // the workspace holds the largest search space the tuner may grow to
     const int m_cap = tuner ? nev + std::max(nex, grown_nex(nex, nev, N)) : m;
@@ -550,6 +561,7 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     CK(cudaMemsetAsync(ctx->sc, 0, sizeof(ChaseScalars), ctx->st));
     Hop op{H, N, ldh, precision_uses_tc(precision)};
     op.bse = bse;
+    op.tri = o.half_storage == 1;
     if ((rc = hop_prepare(ctx, op, m_cap))) return rc;
     GenTcScope gen_scope(ctx, op.tc);
     if ((rc = phase_lanczos(ctx, op, m, o.lanczos_steps, o.lanczos_vecs, o.seed))) return rc;
@@ -955,7 +967,8 @@ int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh,
                              cudaMemcpyHostToDevice, ctx->st));
         h2d += (N - j0) * w * (int64_t)sizeof(z_t);
     }
-    CK(launch_mirror_lower(N, Hd, N, ctx->st));
+    // half storage reads the lower triangle alone: no mirror needed
+    if (!(opts && opts->half_storage == 1)) CK(launch_mirror_lower(N, Hd, N, ctx->st));
     if (ctx->ev_ok) cudaEventRecord(ctx->ev[9], ctx->st);
     rc = solve_device(ctx, (const z_t *)ctx->Hdev.p, N, N, nev, nex, tol, deg_max,
                       precision_mode(precision), opts,
@@ -1119,12 +1132,14 @@ int chase_hemm(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, const
 }
 
 int chase_hemm_slices(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh,
-                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices) {
+                      const void *d_Y, int64_t ldy, int n, void *d_C, int64_t ldc, int slices,
+                      int half_storage) {
     if (!ctx) return BSE_EINVAL;
-    if (!hemm_args_ok(d_H, N, ldh, d_Y, ldy, n, d_C, ldc) || slices < 4 || slices > 6)
+    if (!hemm_args_ok(d_H, N, ldh, d_Y, ldy, n, d_C, ldc) || slices < 4 || slices > 6 ||
+        (half_storage != 0 && half_storage != 1))
         return fail(ctx, BSE_EINVAL, "bad product arguments%s");
-    const Hop op{(const z_t *)d_H, N, ldh, true,
-                 slices == 4 ? OZ_S4 : slices == 5 ? OZ_S5 : OZ_S6};
+    Hop op{(const z_t *)d_H, N, ldh, true, slices == 4 ? OZ_S4 : slices == 5 ? OZ_S5 : OZ_S6};
+    op.tri = half_storage == 1;
     return hemm(ctx, op, n, d_Y, ldy, d_C, ldc);
 }
 

@@ -30,6 +30,7 @@ struct bsechase_ctx {
     DevBuf ozA, ozE, ozB, ozF, ozP;  // tensor-core products: slices of H and of the operand,
                                      // split-K partials
     DevBuf ozGA, ozGE;               // slices and exponents of op(A) for the general products
+    DevBuf ozT;                      // half storage: the row scales t and s = 1 / t
     bool gen_tc = false;             // N x m products of QR and Rayleigh-Ritz on the tensor cores
     int sms = 0;                     // multiprocessors of the device
     uint64_t wait_ns = kDefaultWaitNs;  // bounded waits of the tensor-core kernel

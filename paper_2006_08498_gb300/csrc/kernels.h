@@ -60,15 +60,28 @@ constexpr uint64_t kDefaultWaitNs = 2000000000ull;
 enum OzLevel { OZ_S6 = 0, OZ_S4 = 1, OZ_S5 = 2 };
 inline int oz_pairs(int level) { return level == OZ_S4 ? 10 : level == OZ_S5 ? 15 : 21; }
 
+// The slices of H, prepared once per solve.  Full storage: all Np x Np
+// elements, one exponent per row.  Half storage (tri): the lower-triangle
+// tiles of the symmetrically scaled S = D H D, D = diag(s_i), s_i = 1 / t_i,
+// t_i = sqrt(max_k |H_ik|) (1 + 2^-20), so that S is Hermitian with |S_ik|
+// < 1 and one exponent (0) serves every row; the product reads the upper
+// tiles as the conjugate transposes of the stored ones and computes
+// H Y = T (S (T Y)), T = diag(t_i).
 struct OzakiH {
     int64_t N = 0, Np = 0;
     void *A = nullptr;
     int *E = nullptr;
     uint64_t wait_ns = kDefaultWaitNs;
+    bool tri = false;
+    double *t = nullptr, *s = nullptr;   // tri: t_i and s_i = 1 / t_i (Np each)
     alignas(64) unsigned char tmap[128];
+    alignas(64) unsigned char tmap2[128];   // tri: 64-row boxes of the stored tiles
 };
 int64_t ozaki_padded(int64_t N);
 size_t ozaki_a_bytes(int64_t N);
+// Half storage: the 128 x 64 tiles of the lower triangle, T (T + 1) per
+// part, T = Np / 128.
+size_t ozaki_a_bytes_tri(int64_t N);
 size_t ozaki_b_bytes(int64_t N, int m);
 // workspace for split-K partial products of up to m columns
 size_t ozaki_partial_bytes(int64_t N, int m);
@@ -111,6 +124,11 @@ cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const 
 // Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
 cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,
                             cudaStream_t st);
+// Half storage from the lower triangle of H (the strict upper triangle is
+// never read); oh->A >= ozaki_a_bytes_tri(N), oh->E, oh->t and oh->s hold Np
+// entries each.
+cudaError_t ozaki_prepare_h_tri(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh,
+                                ChaseScalars *sc, cudaStream_t st);
 // C[N x n] = epi(H Y), Y: N x n (ld ldy); bslices >= ozaki_b_bytes(N, n),
 // F >= padded n ints.  GEMM_PLAIN or GEMM_CHEB epilogues (C may alias Yp).
 // level (OzLevel): how many slices of each operand take part.

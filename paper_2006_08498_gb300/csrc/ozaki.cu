@@ -82,9 +82,10 @@ constexpr int kHalf = kN / 2;                         // columns per drain threa
 // FP64 accuracy: (6, 5).  The mixed precision mode's cheaper levels: (4, 5),
 // 32 bits per operand relative to its row/column maximum, every diagonal
 // exact; (5, 5), 40 bits, diagonal 6 in the tail.
-template <int NSL, int EXT>
+template <int NSL, int EXT, bool TRI = false>
 struct OzCfg {
     static constexpr int kSl = NSL;
+    static constexpr bool kTri = TRI;        // half storage of H's slices
     static constexpr bool kTail = EXT < NSL + 1;
     static constexpr int kAcc = (EXT - 1) + (kTail ? 1 : 0);     // TMEM accumulators
     static constexpr int kSmem = kAStages * kATile + (NSL + 1) * kBSlice + 1024;
@@ -93,6 +94,9 @@ struct OzCfg {
 using CfgFP64 = OzCfg<6, 5>;
 using CfgMixed = OzCfg<4, 5>;
 using CfgMid = OzCfg<5, 5>;
+using CfgFP64Tri = OzCfg<6, 5, true>;
+using CfgMixedTri = OzCfg<4, 5, true>;
+using CfgMidTri = OzCfg<5, 5, true>;
 static_assert(CfgFP64::kSmem <= 232448 && CfgFP64::kAcc * kN <= kTmemCols, "resources");
 static_assert(CfgMixed::kSmem <= 232448 && CfgMixed::kAcc * kN <= kTmemCols, "resources");
 static_assert(CfgMid::kSmem <= 232448 && CfgMid::kAcc * kN <= kTmemCols, "resources");
@@ -183,14 +187,15 @@ __global__ void k_row_exponent(int64_t M, int64_t K, const z_t *__restrict__ H, 
     else if (mb > 0) atomicMax(&E[i], frexp_bits(mb));
 }
 
+// With rs, the exponents are those of rs[k] Y[k, j] (half storage: T Y).
 __global__ void k_col_exponent(int64_t N, int n, const z_t *__restrict__ Y, int64_t ldy, int *F,
-                               ChaseScalars *sc) {
+                               ChaseScalars *sc, const double *__restrict__ rs = nullptr) {
     const int j = blockIdx.y;
     if (j >= n) return;
     unsigned long long mb = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const z_t y = Y[k + j * ldy];
+        const z_t y = rs ? zscale(Y[k + j * ldy], rs[k]) : Y[k + j * ldy];
         mb = max(mb, max(abs_bits(y.x), abs_bits(y.y)));
     }
     for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
@@ -271,16 +276,18 @@ __global__ void k_slice_ah(int64_t M, int64_t Mp, int64_t K, int64_t Kp,
 }
 
 // B slices of Y: slice q of Yr, Yi and -Yi (part 0, 1, 2) of column j at
-// tiled_index(q*3 + part, k, j) with mp rows.
+// tiled_index(q*3 + part, k, j) with mp rows.  With rs: the slices of
+// rs[k] Y[k, j] (half storage: T Y).
 __global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__restrict__ Y,
-                          int64_t ldy, const int *__restrict__ F, uint16_t *B) {
+                          int64_t ldy, const int *__restrict__ F, uint16_t *B,
+                          const double *__restrict__ rs = nullptr) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (k >= Np) return;
     z_t y = zmk(0.0, 0.0);
     int e = 0;
     if (j < n && k < N) {
-        y = Y[k + j * ldy];
+        y = rs ? zscale(Y[k + j * ldy], rs[k]) : Y[k + j * ldy];
         e = F[j] == INT_MIN ? 0 : F[j];
     }
     int tr[kS], ti[kS];
@@ -291,6 +298,107 @@ __global__ void k_slice_y(int64_t N, int64_t Np, int n, int mp, const z_t *__res
         B[tiled_index(q * 3 + 0, k, j, Np, mp)] = bf16_exact(slice_value(tr[q], q));
         B[tiled_index(q * 3 + 1, k, j, Np, mp)] = bf16_exact(slice_value(ti[q], q));
         B[tiled_index(q * 3 + 2, k, j, Np, mp)] = bf16_exact(slice_value(-ti[q], q));
+    }
+}
+
+// ---------------------------------------------- half storage of H's slices
+// H = T S T with T = diag(t_i), t_i = sqrt(M_i) (1 + 2^-20), M_i = max_k
+// max(|Re H_ik|, |Im H_ik|): S is Hermitian and |S_ik| <= min(M_i, M_k) /
+// (t_i t_k) < 1, so every row of S is sliced against the one exponent 0 and
+// the digits of S_ki are those of S_ik conjugated.  Only the lower-triangle
+// tiles of S are stored; H Y = T (S (T Y)).
+
+// Row maxima M_i (bit patterns) from the lower triangle: element (i, k),
+// k <= i, counts for row i and, as H_ki = conj(H_ik), for row k.  One
+// 32 x 32 tile (ti >= tj) per CTA; Mx zeroed before.
+__global__ void __launch_bounds__(256)
+k_tri_rowmax(int64_t N, const z_t *__restrict__ H, int64_t ldh, unsigned long long *Mx) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (ti < tj) return;
+    __shared__ unsigned long long rmax[32], cmax[32];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    if (ty == 0) rmax[tx] = cmax[tx] = 0ull;
+    __syncthreads();
+    const int64_t i = (int64_t)ti * 32 + tx;
+    unsigned long long mine = 0;
+    for (int c = ty; c < 32; c += 8) {
+        const int64_t k = (int64_t)tj * 32 + c;
+        if (i >= N || k >= N || k > i) continue;
+        const z_t h = H[i + k * ldh];
+        const unsigned long long mb = max(abs_bits(h.x), abs_bits(h.y));
+        mine = max(mine, mb);
+        atomicMax(&cmax[c], mb);
+    }
+    atomicMax(&rmax[tx], mine);
+    __syncthreads();
+    if (ty == 0) {
+        const int64_t r0 = (int64_t)ti * 32 + tx, r1 = (int64_t)tj * 32 + tx;
+        if (r0 < N && rmax[tx]) atomicMax(&Mx[r0], rmax[tx]);
+        if (r1 < N && cmax[tx]) atomicMax(&Mx[r1], cmax[tx]);
+    }
+}
+
+// t_i, s_i = 1 / t_i (1 for an all-zero or padded row) and E_i = 0
+// (INT_MIN for padded rows).  Mx may alias s (each thread reads its own
+// entry before writing it).  Non-finite rows set DEV_NONFINITE.
+__global__ void k_tri_scales(int64_t N, int64_t Np, const unsigned long long *Mx, double *t,
+                             double *s, int *E, ChaseScalars *sc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Np) return;
+    double ti = 1.0;
+    if (i < N) {
+        const unsigned long long mb = Mx[i];
+        if (mb >= kNonFinite) set_error(sc, DEV_NONFINITE, (int)i);
+        else if (mb > 0) ti = sqrt(__longlong_as_double((long long)mb)) * (1.0 + 0x1.0p-20);
+    }
+    t[i] = ti;
+    s[i] = 1.0 / ti;
+    E[i] = i < N ? 0 : INT_MIN;
+}
+
+// Offset of element (row r, column c) of stored tile `slot` of part `part`
+// (128 x 64, row-major).
+__host__ __device__ __forceinline__ int64_t tri_index(int part, int64_t slot, int64_t nslots, int r, int c) {
+    return ((part * nslots + slot) * kBM + r) * kKC + c;
+}
+
+// Slices of S into the stored tiles: tile (b, kc) of 128 rows x 64 columns,
+// kc <= 2 b + 1, is slot b (b + 1) + kc of each part (Re and Im of slice p:
+// parts 2p and 2p + 1).  The elements above the diagonal (in the tiles that
+// straddle it) are the conjugates of their mirrors, so the strict upper
+// triangle of H is never read; zeros outside N.  32 x 32 tiles through
+// shared memory (tk: column tile, ti: row tile), coalesced both ways.
+__global__ void __launch_bounds__(256)
+k_slice_tri(int64_t N, const z_t *__restrict__ H, int64_t ldh, const double *__restrict__ s,
+            int64_t nslots, uint16_t *A) {
+    const int tk = blockIdx.x, ti = blockIdx.y;
+    const int b = ti / (kBM / 32), kc = tk / (kKC / 32);
+    if (kc > 2 * b + 1) return;
+    __shared__ z_t tile[32][33];                   // tile[c][r] = S(i0 + r, k0 + c)
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int64_t i0 = (int64_t)ti * 32, k0 = (int64_t)tk * 32;
+    for (int c = ty; c < 32; c += 8) {
+        const int64_t i = i0 + tx, k = k0 + c;
+        z_t h = zmk(0.0, 0.0);
+        if (i < N && k < N) {
+            h = (k <= i) ? H[i + k * ldh] : zconj(H[k + i * ldh]);
+            h = zscale(h, s[i] * s[k]);
+        }
+        tile[c][tx] = h;
+    }
+    __syncthreads();
+    const int64_t slot = (int64_t)b * (b + 1) + kc;
+    for (int r = ty; r < 32; r += 8) {
+        const z_t h = tile[tx][r];                 // S(i0 + r, k0 + tx)
+        const int row = (int)(i0 + r - (int64_t)b * kBM), col = (int)(k0 + tx - (int64_t)kc * kKC);
+        int tr[kS], tim[kS];
+        split_digits(h.x, 0, tr);
+        split_digits(h.y, 0, tim);
+#pragma unroll
+        for (int p = 0; p < kS; p++) {
+            A[tri_index(2 * p, slot, nslots, row, col)] = bf16_exact(slice_value(tr[p], p));
+            A[tri_index(2 * p + 1, slot, nslots, row, col)] = bf16_exact(slice_value(tim[p], p));
+        }
     }
 }
 
@@ -431,6 +539,7 @@ struct OzArgs {
     int tx, ty, tz;   // work units: column tiles x row tiles x splits
     unsigned long long *P;   // raw partials of the splits, layout below
     uint64_t wait_ns;        // limit of each bounded mbarrier wait
+    int nslots;              // half storage: stored tiles per part, T (T + 1)
 };
 
 // One launch of the product kernel runs the work units of up to kMaxJobs
@@ -441,6 +550,7 @@ struct OzArgs {
 constexpr int kMaxJobs = 8;
 struct OzJob {
     CUtensorMap tmA, tmB;    // slices of op(A) and of Y
+    CUtensorMap tmA2;        // half storage: 64-row boxes of the stored tiles
     OzArgs args;
     int unit0;               // first unit of this job in the launch
 };
@@ -592,6 +702,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                   "FirstPassOrder and the barrier groups assume kEx = 5 and 4 <= S <= 6");
     constexpr int kNEx = kEx - 1;              // exact accumulators
     constexpr bool kTail = Cfg::kTail;
+    constexpr bool kTri = Cfg::kTri;
     constexpr int kNB = S + 1;                 // B buffers: slices 1..S, slice 1 twice
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -670,6 +781,7 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
             for (int j = 0; j < bt.njobs; j++) {
                 tc::prefetch_tmap(&bt.job[j].tmA);
                 tc::prefetch_tmap(&bt.job[j].tmB);
+                if (kTri) tc::prefetch_tmap(&bt.job[j].tmA2);
             }
             constexpr ProducerOrder<S> order;
             bool ok = true;
@@ -679,9 +791,15 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                 int64_t i0;
                 unit(u, jb, j0, i0, z, c0, c1);
                 const CUtensorMap *tmA = &bt.job[jb].tmA, *tmB = &bt.job[jb].tmB;
-                const int nch = bt.job[jb].args.nchunks;
+                const CUtensorMap *tmA2 = &bt.job[jb].tmA2;
+                const int nch = bt.job[jb].args.nchunks, ns = bt.job[jb].args.nslots;
+                const int br = (int)(i0 / kBM);           // row tile
                 for (int c = c0; c < c1 && ok; c++, gc++) {
                     ab_gc = gc;
+                    // half storage: chunk c lies above the stored triangle of
+                    // row tile br, so its A tile is read from the stored tiles
+                    // (c / 2, 2 br) and (c / 2, 2 br + 1), rows 64 (c % 2) on
+                    const bool mir = kTri && c > 2 * br + 1;
 #pragma unroll
                     for (int it = 0; it < 2 * S; it++) {
                         if (order.kind[it] == 0) {
@@ -696,8 +814,22 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                             // parts (slice p, re) and (slice p, im) = 2 pp, 2 pp + 1 in the
                             // A tensor's part order
                             uint8_t *adst = sA + st * 2 * kATile;
-                            tc::tma_load_3d(adst, tmA, 0, (int)i0, (2 * pp) * nch + c, &fullA[st]);
-                            tc::tma_load_3d(adst + kATile, tmA, 0, (int)i0, (2 * pp + 1) * nch + c, &fullA[st]);
+                            if (!kTri) {
+                                tc::tma_load_3d(adst, tmA, 0, (int)i0, (2 * pp) * nch + c, &fullA[st]);
+                                tc::tma_load_3d(adst + kATile, tmA, 0, (int)i0, (2 * pp + 1) * nch + c, &fullA[st]);
+                            } else if (!mir) {
+                                const int zt = br * (br + 1) + c;            // stored tile (br, c)
+                                tc::tma_load_3d(adst, tmA, 0, 0, (2 * pp) * ns + zt, &fullA[st]);
+                                tc::tma_load_3d(adst + kATile, tmA, 0, 0, (2 * pp + 1) * ns + zt, &fullA[st]);
+                            } else {
+                                const int bc = c >> 1, zt = bc * (bc + 1) + 2 * br, y = (c & 1) * 64;
+#pragma unroll
+                                for (int r = 0; r < 2; r++) {
+                                    uint8_t *d = adst + r * kATile;
+                                    tc::tma_load_3d(d, tmA2, 0, y, (2 * pp + r) * ns + zt, &fullA[st]);
+                                    tc::tma_load_3d(d + kATile / 2, tmA2, 0, y, (2 * pp + r) * ns + zt + 1, &fullA[st]);
+                                }
+                            }
                         } else {
                             const int q = order.idx[it];
                             const int b = bbuf(q, gc), n = buse(q, gc);
@@ -730,6 +862,12 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
             // offsets in 16-byte units of the 14-bit address field (the whole
             // operand area lies below 256 KB, so no carry leaves the field)
             const uint64_t adesc0 = tc::sdesc_sw128(sA), bdesc0 = tc::sdesc_sw128(sB);
+            // half storage, chunks above the stored triangle: the two 64-row
+            // halves of each A tile read MN-major (transposed), the Im pass
+            // negated (the tile is conj(H) transposed)
+            const uint64_t adescT0 = tc::sdesc_sw128_mn(sA, kATile / 2);
+            constexpr uint32_t idescT = idesc | tc::kIdescTransA;
+            constexpr uint32_t idescTN = idescT | tc::kIdescNegA;
             constexpr FirstPassOrder<S> kFirst;
             bool ok = true;
             int gc = 0, uc = 0, ts = 0;   // ts: unit tails committed
@@ -737,9 +875,11 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                 int jb, j0, z, c0, c1;
                 int64_t i0;
                 unit(u, jb, j0, i0, z, c0, c1);
+                const int br = (int)(i0 / kBM);
                 for (int c = c0; c < c1 && ok; c++, gc++) {
                     const int cl = c - c0, nc = c1 - c0;
                     const bool first = cl == 0;   // the unit's first chunk
+                    const bool mir = kTri && c > 2 * br + 1;
 #pragma unroll
                     for (int pi = 0; pi < S2; pi++) {
                         const int p = pi / 2 + 1, ri = pi & 1;
@@ -748,7 +888,11 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                             if (!tc::mbar_wait(&fullA[st], (ua / kAPairs) & 1, &abort_flag, wait_ns)) { ok = false; break; }
                             tc::fence_after();
                         }
-                        const uint64_t a0 = adesc0 + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
+                        const uint64_t a0 = (mir ? adescT0 : adesc0) + (uint64_t)((st * 2 * kATile + ri * kATile) >> 4);
+                        // K step of 16: 32 bytes along a K-major row, 16 rows of
+                        // 128 bytes MN-major
+                        const uint32_t ak = mir ? 128u : 2u;
+                        const uint32_t id = !mir ? idesc : (ri == 0 ? idescT : idescTN);
                         // One MMA: K step kk of slice pair (p, q).
                         // coll: the A-collector use of the first pass (0: none)
                         auto step = [&](int kk, int q, int coll) -> bool {
@@ -779,19 +923,19 @@ k_ozaki_zgemm(const __grid_constant__ OzBatch bt) {
                             const bool fresh = (g <= kEx) ? (pi == 0 && q == g - 1 && cl % drain_period(g) == 0)
                                                           : (first && pi == 0 && q == S);
                             const uint32_t acc = (fresh && kk == 0) ? 0u : 1u;
-                            const uint64_t a = a0 + 2 * kk, bd = b0 + 2 * kk;
+                            const uint64_t a = a0 + ak * kk, bd = b0 + 2 * kk;
                             if (pi == 0 && coll == tc::A_FILL)
-                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, id, acc);
                             else if (pi == 0 && coll == tc::A_LASTUSE)
-                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, id, acc);
                             else if (pi == 0 || p == S)
-                                tc::mma_bf16(d, a, bd, idesc, acc);
+                                tc::mma_bf16(d, a, bd, id, acc);
                             else if (q == S + 1 - p)
-                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, idesc, acc);
+                                tc::mma_bf16_ca<tc::A_FILL>(d, a, bd, id, acc);
                             else if (q == 1)
-                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, idesc, acc);
+                                tc::mma_bf16_ca<tc::A_LASTUSE>(d, a, bd, id, acc);
                             else
-                                tc::mma_bf16_ca<tc::A_USE>(d, a, bd, idesc, acc);
+                                tc::mma_bf16_ca<tc::A_USE>(d, a, bd, id, acc);
                             return true;
                         };
                         if (pi == 0) {
@@ -1032,13 +1176,16 @@ __device__ __forceinline__ z_t recombine(const unsigned long long *__restrict__ 
 __device__ __forceinline__ int exp_or_zero(int e) { return e == INT_MIN ? 0 : e; }
 
 // C = epi(H Y) from the splits' partials (summed in increasing z: deterministic).
+// With ts (half storage): row i of the recombined product scaled by ts[i].
 __global__ void k_split_reduce(int64_t M, int n, int nsplit, const unsigned long long *__restrict__ P,
                                const int *__restrict__ E, const int *__restrict__ F, GemmEpi ep,
-                               const z_t *__restrict__ Y, int64_t ldy, z_t *C, int64_t ldc) {
+                               const z_t *__restrict__ Y, int64_t ldy, z_t *C, int64_t ldc,
+                               const double *__restrict__ ts) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= M) return;
     z_t v = recombine(P, nsplit, n, j, M, i, exp_or_zero(E[i]) + exp_or_zero(F[j]));
+    if (ts) v = zscale(v, ts[i]);
     if (ep.mode == GEMM_CHEB) {
         v = zscale(zsub(v, zscale(Y[i + j * ldy], ep.c)), ep.s1);
         if (ep.Yp) v = zsub(v, zscale(ep.Yp[i + j * ep.ldyp], ep.s2));
@@ -1143,6 +1290,11 @@ size_t ozaki_a_bytes(int64_t N) {
     return (size_t)kS * 2 * Np * Np * 2;
 }
 
+size_t ozaki_a_bytes_tri(int64_t N) {
+    const int64_t T = ozaki_padded(N) / kBM;
+    return (size_t)kS * 2 * T * (T + 1) * kBM * kKC * 2;
+}
+
 size_t ozaki_partial_bytes(int64_t N, int m) {
     const int mp = (m + kW - 1) / kW * kW;
     // splits x columns: the minimum split count of a product with K = N at
@@ -1164,6 +1316,7 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     const int64_t Np = ozaki_padded(N);
     oh->N = N;
     oh->Np = Np;
+    oh->tri = false;
     k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
     bse_count_launches(1);
     const int cpb = 256;
@@ -1179,6 +1332,26 @@ cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, Ch
     return cudaGetLastError();
 }
 
+cudaError_t ozaki_prepare_h_tri(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh,
+                                ChaseScalars *sc, cudaStream_t st) {
+    const int64_t Np = ozaki_padded(N), T = Np / kBM, nslots = T * (T + 1);
+    oh->N = N;
+    oh->Np = Np;
+    oh->tri = true;
+    unsigned long long *Mx = (unsigned long long *)oh->s;
+    cudaError_t e = cudaMemsetAsync(Mx, 0, (size_t)Np * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const unsigned Tt = (unsigned)((N + 31) / 32), Tp = (unsigned)(Np / 32);
+    k_tri_rowmax<<<dim3(Tt, Tt), dim3(32, 8), 0, st>>>(N, H, ldh, Mx);
+    k_tri_scales<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(N, Np, Mx, oh->t, oh->s, oh->E, sc);
+    k_slice_tri<<<dim3(Tp, Tp), dim3(32, 8), 0, st>>>(N, H, ldh, oh->s, nslots, (uint16_t *)oh->A);
+    bse_count_launches(3);
+    if (!make_map((CUtensorMap *)oh->tmap, oh->A, kBM, (uint64_t)(kS * 2 * nslots), kBM) ||
+        !make_map((CUtensorMap *)oh->tmap2, oh->A, kBM, (uint64_t)(kS * 2 * nslots), kBM / 2))
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const double *dE,
                               const z_t *u, const z_t *a, const double *Kt, OzakiH *oh,
                               ChaseScalars *sc, cudaStream_t st) {
@@ -1186,6 +1359,7 @@ cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const 
     const int64_t Np = ozaki_padded(N);
     oh->N = N;
     oh->Np = Np;
+    oh->tri = false;
     k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
     bse_count_launches(1);
     const int dyn = 2 * kGT * std::max(md.rank_x, 1) * (int)sizeof(z_t);
@@ -1223,10 +1397,16 @@ cudaError_t launch_variant(const OzBatch &b, int sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const OzBatch &b, int level, int sms, cudaStream_t st) {
-    switch (level) {
+// Kernel configuration of a launch: the accuracy level (OzLevel), plus
+// kOzTri for half storage.
+constexpr int kOzTri = 4;
+cudaError_t launch_batch(const OzBatch &b, int cfg, int sms, cudaStream_t st) {
+    switch (cfg) {
     case OZ_S4: return launch_variant<CfgMixed>(b, sms, st);
     case OZ_S5: return launch_variant<CfgMid>(b, sms, st);
+    case OZ_S6 | kOzTri: return launch_variant<CfgFP64Tri>(b, sms, st);
+    case OZ_S4 | kOzTri: return launch_variant<CfgMixedTri>(b, sms, st);
+    case OZ_S5 | kOzTri: return launch_variant<CfgMidTri>(b, sms, st);
     default: return launch_variant<CfgFP64>(b, sms, st);
     }
 }
@@ -1435,16 +1615,18 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     const int mp = (n + kW - 1) / kW * kW;
     k_fill_int<<<(mp + 255) / 256, 256, 0, st>>>(F, mp, INT_MIN);
     bse_count_launches(1);
+    // half storage: the slices of T Y (H Y = T (S (T Y)))
+    const double *rs = oh.tri ? oh.t : nullptr;
     dim3 ge((unsigned)std::min<int64_t>((N + 255) / 256, 16), (unsigned)n);
-    k_col_exponent<<<ge, 256, 0, st>>>(N, n, Y, ldy, F, sc);
+    k_col_exponent<<<ge, 256, 0, st>>>(N, n, Y, ldy, F, sc, rs);
     bse_count_launches(1);
     dim3 gs((unsigned)((Np + 255) / 256), (unsigned)mp);
-    k_slice_y<<<gs, 256, 0, st>>>(N, Np, n, mp, Y, ldy, F, (uint16_t *)bslices);
+    k_slice_y<<<gs, 256, 0, st>>>(N, Np, n, mp, Y, ldy, F, (uint16_t *)bslices, rs);
     bse_count_launches(1);
     CUtensorMap tmB;
     if (!make_map(&tmB, bslices, (uint64_t)mp, (uint64_t)(kS * 3 * (Np / kKC)), kW))
         return cudaErrorInvalidValue;
-    OzArgs a;
+    OzArgs a{};
     a.M = N;
     a.n = n;
     a.mp = mp;
@@ -1462,19 +1644,23 @@ cudaError_t ozaki_zgemm(const OzakiH &oh, int n, const z_t *Y, int64_t ldy, z_t 
     a.tx = tx;
     a.ty = ty;
     a.tz = nsplit;
+    a.nslots = oh.tri ? (int)((Np / kBM) * (Np / kBM + 1)) : 0;
     const CUtensorMap &tmA = *(const CUtensorMap *)oh.tmap;
-    const OzBatch one = single(tmA, tmB, a);
+    OzBatch one = single(tmA, tmB, a);
+    if (oh.tri) one.job[0].tmA2 = *(const CUtensorMap *)oh.tmap2;
+    const int cfg = level | (oh.tri ? kOzTri : 0);
     cudaError_t e;
     if (batcher) {
-        e = ozb_run(batcher, one.job[0], level, st);   // launched with other solvers' products
+        e = ozb_run(batcher, one.job[0], cfg, st);   // launched with other solvers' products
     } else {
         if (ev0) cudaEventRecord(ev0, st);
-        e = launch_batch(one, level, sms, st);
+        e = launch_batch(one, cfg, sms, st);
         if (ev1) cudaEventRecord(ev1, st);
     }
     if (e != cudaSuccess) return e;
     dim3 gr((unsigned)((N + 255) / 256), (unsigned)n);
-    k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, a.P, a.E, a.F, ep, Y, ldy, C, ldc);
+    k_split_reduce<<<gr, 256, 0, st>>>(N, n, nsplit, a.P, a.E, a.F, ep, Y, ldy, C, ldc,
+                                       oh.tri ? oh.t : nullptr);
     bse_count_launches(1);
     return cudaGetLastError();
 }
@@ -1526,7 +1712,7 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
     if (!make_map(&tmA, w.A, (uint64_t)Mp, (uint64_t)(kS * 2 * (Kp / kKC)), kBM) ||
         !make_map(&tmB, w.B, (uint64_t)mp, (uint64_t)(kS * 3 * (Kp / kKC)), kW))
         return cudaErrorInvalidValue;
-    OzArgs a;
+    OzArgs a{};
     a.M = M;
     a.n = n;
     a.mp = mp;

@@ -105,11 +105,25 @@ __device__ __forceinline__ uint64_t sdesc_sw128(const void *p) {
            (2ull << 61);
 }
 
+// Shared-memory matrix descriptor: MN-major operand, 128-byte swizzle.  Each
+// 128-byte row holds 64 consecutive MN elements of one K index; 8-row groups
+// (K) are 1024 bytes apart (SBO) and the 64-element groups of MN `lbo` bytes
+// apart (LBO).  The same bytes a K-major tile load leaves in shared memory,
+// read transposed.
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(const void *p, uint32_t lbo) {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor bits: negate A, A MN-major (transposed).
+constexpr uint32_t kIdescNegA = 1u << 13;
+constexpr uint32_t kIdescTransA = 1u << 15;
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {

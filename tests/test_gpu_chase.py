@@ -159,6 +159,53 @@ def test_hemm_slice_levels(ctx):
         assert ei.value.status == pkg.BSE_EINVAL
 
 
+@pytest.mark.parametrize("n,m,seed", [(333, 7, 1), (1000, 40, 2), (129, 33, 3), (64, 1, 4),
+                                      (640, 96, 5)])
+def test_hemm_half_storage(ctx, n, m, seed):
+    """The product on the slices of H's lower triangle: row tiles read the
+    tiles above the stored triangle transposed and conjugated.  Same bound as
+    the full product, at shapes with one to eight row tiles and ragged
+    edges; NaN in the strict upper triangle is never read."""
+    A, _ = hermitian(n, seed)
+    Y = block(n, m, seed + 1)
+    Y[:, 0] *= 1e-9
+    if m > 2:
+        Y[:, 2] *= 3e7
+        Y[5, 1] = 1e5
+    Ag = A.copy()
+    Ag[np.triu_indices(n, 1)] = np.nan
+    C = host(ctx.hemm(dev(Ag), dev(Y), half_storage=True))
+    assert np.max(colwise_err(C, A, Y)) <= EMUL_TOL
+    if n >= 300:
+        # the slice levels of the mixed mode on half storage
+        e4 = np.max(colwise_err(host(ctx.hemm(dev(Ag), dev(Y), slices=4, half_storage=True)), A, Y))
+        e5 = np.max(colwise_err(host(ctx.hemm(dev(Ag), dev(Y), slices=5, half_storage=True)), A, Y))
+        assert e4 <= 1e-7 and e5 <= 5e-10 and e4 >= 30 * e5
+
+
+def test_hemm_half_storage_graded_rows(ctx):
+    """Rows and columns of very different size (D A D, D from 1e-3 to 1e3):
+    the symmetric scaling keeps the normwise bound.  Row by row it is
+    relative to sqrt(M_i max_k M_k) instead of the row's own maximum M_i, so
+    the small rows of a graded matrix are less accurate than with full
+    storage (checked here against the full product's row-wise error)."""
+    n = 400
+    A, _ = hermitian(n, 11)
+    d = np.logspace(-3, 3, n)
+    A = d[:, None] * A * d[None, :]
+    Y = block(n, 20, 12)
+    C = host(ctx.hemm(dev(A), dev(Y), half_storage=True))
+    Cf = host(ctx.hemm(dev(A), dev(Y)))
+    assert np.max(colwise_err(C, A, Y)) <= EMUL_TOL
+    assert np.max(colwise_err(Cf, A, Y)) <= EMUL_TOL
+    scale = np.abs(A) @ np.abs(Y)                  # row i's own size
+    ref = A @ Y
+    row_half = np.max(np.abs(C - ref) / scale, axis=1)
+    row_full = np.max(np.abs(Cf - ref) / scale, axis=1)
+    assert np.max(row_full) <= 1e-10
+    assert np.max(row_half[:20]) > np.max(row_full[:20])   # the smallest rows
+
+
 def test_hemm_zero_column_and_bse_matrix(ctx):
     H = oracle.build_h(0, 125, 4, 4)
     Y = block(2000, 75, 9)
@@ -380,6 +427,38 @@ def test_solve_c1_matches_oracle(ctx, c1, precision):
     assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[precision], atol=0)
     assert abs(st["iters"] - ref["iters"]) <= 1
     assert st["iters"] >= 2
+
+
+@pytest.mark.parametrize("precision", [pkg.CHASE_FP64, pkg.CHASE_MIXED_FP32])
+def test_solve_half_storage(ctx, c1, precision):
+    """C1 on the slices of H's lower triangle (chase_opts.half_storage): the
+    dense oracle's eigenpairs at the FP64 tolerances, iterations within one
+    of the oracle's ChASE, eigenvalues within a few 1e-12 of the full-storage
+    solve; from host buffers with NaN above the diagonal, bit for bit the
+    device solve."""
+    H, w, ref = c1
+    Hd = ctx.build_hamiltonian(0, 125, 4, 4)
+    ef, _, _, _ = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, precision=precision)
+    evals, Vd, resid, st = ctx.solve(Hd, 50, 25, tol=1e-10, deg_max=36, precision=precision,
+                                     half_storage=True)
+    _check_solution(H, evals, host(Vd), resid, 50, w_exact=w, ref=ref["evecs"])
+    assert np.max(resid) <= 1e-10
+    assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[pkg.CHASE_FP64], atol=0)
+    assert abs(st["iters"] - ref["iters"]) <= 1
+    assert np.max(np.abs(evals - ef) / np.abs(ef)) <= 5e-12
+    N = H.shape[0]
+    e1, V1, r1, _ = ctx.solve(dev(H), 50, 25, tol=1e-10, deg_max=36, precision=precision,
+                              half_storage=True)
+    Hg = pkg.host_empty((N, N))
+    Hg[:] = H
+    Hg[np.triu_indices(N, 1)] = np.nan
+    e2, V2, r2, _ = ctx.solve_host(Hg, 50, 25, tol=1e-10, deg_max=36, precision=precision,
+                                   half_storage=True)
+    assert np.array_equal(e2, e1) and np.array_equal(r2, r1)
+    assert np.array_equal(V2, host(V1))
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.solve(Hd, 50, 25, precision=pkg.CHASE_FP64_DFMA, half_storage=True)
+    assert ei.value.status == pkg.BSE_EINVAL
 
 
 def test_solve_mixed_precision(ctx, c1):
