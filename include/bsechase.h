@@ -134,8 +134,10 @@ typedef struct {
                             H = T S T with t_i = sqrt(max_k |H_ik|), so that
                             one exponent serves S's rows and its columns, and
                             the product reads each stored tile of S both
-                            ways.  Tensor-core precisions and chase_solve /
-                            chase_solve_host only (BSE_EINVAL otherwise). */
+                            ways.  Tensor-core precisions only (BSE_EINVAL
+                            otherwise).  With chase_solve_bse the slices are
+                            generated, so H's whole footprint is 12 N^2
+                            bytes. */
 } chase_opts;
 
 /* Per-solve statistics (times in milliseconds, CUDA events on the stream). */
@@ -230,7 +232,8 @@ int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int 
  * (same seed, Nk, Nv, Nc, model), without storing it: its elements are
  * generated straight into the tensor-core slices of H, so the N x N
  * complex128 matrix (16 N^2 bytes) never exists and the device memory the
- * solve needs drops from 40 N^2 to 24 N^2 bytes plus workspace (Sec. 3's
+ * solve needs drops from 40 N^2 to 24 N^2 bytes plus workspace, 12 N^2 with
+ * chase_opts.half_storage (Sec. 3's
  * filter works on H only through its products).  The slices, and so every
  * result, are bit for bit those of bse_build_hamiltonian + chase_solve.
  * Tensor-core precisions only (CHASE_FP64, CHASE_MIXED_FP32, value 2);

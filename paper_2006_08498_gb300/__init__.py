@@ -358,9 +358,11 @@ class Context:
 
     def solve_bse(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
                   model=None, deg_init=20, max_iter=50, lanczos_steps=25, lanczos_vecs=4,
-                  seed_start=0, evecs=None, degree_group=0, nex_damping=0.0):
+                  seed_start=0, evecs=None, degree_group=0, nex_damping=0.0,
+                  half_storage=False):
         """Lowest nev eigenpairs of the synthetic Hamiltonian (seed, Nk, Nv,
-        Nc, model) without storing it (chase_solve_bse).  seed_start seeds the
+        Nc, model) without storing it (chase_solve_bse; with half_storage only
+        the lower triangle's slices are made).  seed_start seeds the
         Lanczos and start vectors (`seed` of solve()).  Returns (evals, evecs
         tensor N x nev, resid, stats)."""
         torch = self._torch
@@ -376,7 +378,7 @@ class Context:
                     int(md["rank_x"]))
         st = Stats()
         o = self._opts(deg_init, max_iter, lanczos_steps, lanczos_vecs, seed_start, None,
-                       degree_group, nex_damping)
+                       degree_group, nex_damping, half_storage)
         rc = load().chase_solve_bse(self._h, seed, Nk, Nv, Nc, ctypes.byref(mdl), nev, nex, tol,
                                     deg_max, precision, ctypes.byref(o), _dp(evals),
                                     ctypes.c_void_p(evecs.data_ptr()), _ld(evecs), _dp(resid),

@@ -210,11 +210,11 @@ int hop_prepare(bsechase_ctx *ctx, Hop &op, int max_cols) {
     ctx->oh.wait_ns = ctx->wait_ns;
     ctx->oh.t = (double *)ctx->ozT.p;
     ctx->oh.s = ctx->oh.t ? ctx->oh.t + Np : nullptr;
-    if (op.tri && !op.bse)
-        CK(ozaki_prepare_h_tri(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
-    else if (op.bse)
+    if (op.bse)
         CK(ozaki_prepare_bse(op.bse->Nk, op.bse->Nv, op.bse->Nc, op.bse->md, op.bse->dE, op.bse->u,
-                             op.bse->a, op.bse->Kt, &ctx->oh, ctx->sc, ctx->st));
+                             op.bse->a, op.bse->Kt, op.tri, &ctx->oh, ctx->sc, ctx->st));
+    else if (op.tri)
+        CK(ozaki_prepare_h_tri(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
     else
         CK(ozaki_prepare_h(op.N, op.H, op.ldh, &ctx->oh, ctx->sc, ctx->st));
     return BSE_OK;
@@ -542,9 +542,8 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
     if (o.degree_group < 0) return fail(ctx, BSE_EINVAL, "degree_group must be >= 0%s");
     if (!(o.nex_damping >= 0.0 && o.nex_damping < 1.0))
         return fail(ctx, BSE_EINVAL, "nex_damping must be in [0, 1)%s");
-    if (o.half_storage != 0 && (o.half_storage != 1 || !precision_uses_tc(precision) || bse))
-        return fail(ctx, BSE_EINVAL,
-                    "half_storage = 1 needs a tensor-core precision and a stored H%s");
+    if (o.half_storage != 0 && (o.half_storage != 1 || !precision_uses_tc(precision)))
+        return fail(ctx, BSE_EINVAL, "half_storage = 1 needs a tensor-core precision%s");
     const bool tuner = o.nex_damping > 0.0;
     // the workspace holds the largest search space the tuner may grow to
     const int m_cap = tuner ? nev + std::max(nex, grown_nex(nex, nev, N)) : m;

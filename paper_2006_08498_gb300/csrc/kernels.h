@@ -118,8 +118,10 @@ cudaError_t ozaki_gemm(int64_t M, int n, int64_t K, const z_t *A, int64_t lda, i
 // tables (launch_bse_tables) without storing H; oh->A and oh->E must hold
 // ozaki_a_bytes(N) and Np ints.  The values are those bse_build_hamiltonian
 // writes, bit for bit.
+// With tri: half storage (the layout of ozaki_prepare_h_tri; oh->t and oh->s
+// hold Np entries each), bit for bit ozaki_prepare_h_tri on the built H.
 cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const double *dE,
-                              const z_t *u, const z_t *a, const double *Kt, OzakiH *oh,
+                              const z_t *u, const z_t *a, const double *Kt, bool tri, OzakiH *oh,
                               ChaseScalars *sc, cudaStream_t st);
 // Non-finite entries of H (or of a product's operand) set DEV_NONFINITE in sc.
 cudaError_t ozaki_prepare_h(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh, ChaseScalars *sc,

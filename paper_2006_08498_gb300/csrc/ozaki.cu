@@ -430,11 +430,13 @@ __device__ __forceinline__ void stage_tile(int i0, int j0, int N, int R, const z
     }
 }
 
-// Row exponents: E[i] = frexp exponent of max_k max(|Re H_ik|, |Im H_ik|).
+// Row exponents: E[i] = frexp exponent of max_k max(|Re H_ik|, |Im H_ik|);
+// with Mx (half storage) the maxima themselves, as bit patterns.
 __global__ void __launch_bounds__(256)
 k_gen_row_exponent(int Nk, int nb, int N, BseModel md, const double *__restrict__ dE,
                    const z_t *__restrict__ u, const z_t *__restrict__ a,
-                   const double *__restrict__ Kt, int *E, ChaseScalars *sc) {
+                   const double *__restrict__ Kt, int *E, ChaseScalars *sc,
+                   unsigned long long *Mx) {
     const int ti = blockIdx.x, tj = blockIdx.y;
     if (ti < tj) return;
     extern __shared__ z_t gsm[];
@@ -466,7 +468,8 @@ k_gen_row_exponent(int Nk, int nb, int N, BseModel md, const double *__restrict_
         const int row[2] = {i0 + tx, j0 + tx};
         for (int k = 0; k < 2; k++) {
             if (row[k] >= N || m[k] == 0) continue;
-            if (m[k] >= kNonFinite) set_error(sc, DEV_NONFINITE, row[k]);
+            if (Mx) atomicMax(&Mx[row[k]], m[k]);      // k_tri_scales checks finiteness
+            else if (m[k] >= kNonFinite) set_error(sc, DEV_NONFINITE, row[k]);
             else atomicMax(&E[row[k]], frexp_bits(m[k]));
         }
     }
@@ -522,6 +525,62 @@ k_gen_slice(int Nk, int nb, int N, int64_t Np, BseModel md, const double *__rest
                 A[tiled_index(p * 2 + 0, k, i, Np, Np)] = bf16_exact(slice_value(tr[p], p));
                 A[tiled_index(p * 2 + 1, k, i, Np, Np)] = bf16_exact(slice_value(tim[p], p));
             }
+        }
+    }
+}
+
+// Half storage of the synthetic H, H not stored: the slices of S = D H D
+// (k_slice_tri's layout) with the elements generated.  Sub-tile (ti, tk) of
+// 32 x 32 is computed from the lower tile of its pair, L = H(hi.., lo..), hi
+// = max(ti, tk), lo = min(ti, tk): directly below the diagonal, conjugated
+// and transposed above it.
+__global__ void __launch_bounds__(256)
+k_gen_slice_tri(int Nk, int nb, int N, BseModel md, const double *__restrict__ dE,
+                const z_t *__restrict__ u, const z_t *__restrict__ a, const double *__restrict__ Kt,
+                const double *__restrict__ s, int64_t nslots, uint16_t *A) {
+    const int tk = blockIdx.x, ti = blockIdx.y;
+    const int b = ti / (kBM / kGT), kc = tk / (kKC / kGT);
+    if (kc > 2 * b + 1) return;
+    extern __shared__ z_t gsm[];
+    __shared__ z_t lt[kGT][kGT + 1];               // lt[r][c] = H(hi0 + r, lo0 + c)
+    __shared__ z_t ui[kGT], uj[kGT];
+    __shared__ double dEi[kGT];
+    const int R = md.rank_x;
+    z_t *sai = gsm, *saj = gsm + kGT * R;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int hi = max(ti, tk), lo = min(ti, tk);
+    const int hi0 = hi * kGT, lo0 = lo * kGT;
+    stage_tile(hi0, lo0, N, R, a, u, dE, sai, saj, ui, uj, dEi);
+    __syncthreads();
+    for (int c = ty; c < kGT; c += 8) {
+        const int I = hi0 + tx, J = lo0 + c;
+        z_t h = zmk(0.0, 0.0);
+        if (!(hi == lo && tx < c) && I < N && J < N)
+            h = bse_element(I, J, R, sai + tx, saj + c, kGT, ui[tx], uj[c], dEi[tx], Nk, nb, md.w0,
+                            Kt);
+        lt[tx][c] = h;
+    }
+    __syncthreads();
+    if (hi == lo)                                  // the upper half of a diagonal tile
+        for (int c = ty; c < kGT; c += 8)
+            if (tx < c) lt[tx][c] = zconj(lt[c][tx]);
+    __syncthreads();
+    const int64_t slot = (int64_t)b * (b + 1) + kc;
+    for (int r = ty; r < kGT; r += 8) {
+        const int i = ti * kGT + r, k = tk * kGT + tx;   // row i, consecutive k
+        z_t h = zmk(0.0, 0.0);
+        if (i < N && k < N) {
+            h = ti >= tk ? lt[r][tx] : zconj(lt[tx][r]);
+            h = zscale(h, s[i] * s[k]);
+        }
+        const int row = i - b * kBM, col = k - kc * kKC;
+        int tr[kS], tim[kS];
+        split_digits(h.x, 0, tr);
+        split_digits(h.y, 0, tim);
+#pragma unroll
+        for (int p = 0; p < kS; p++) {
+            A[tri_index(2 * p, slot, nslots, row, col)] = bf16_exact(slice_value(tr[p], p));
+            A[tri_index(2 * p + 1, slot, nslots, row, col)] = bf16_exact(slice_value(tim[p], p));
         }
     }
 }
@@ -1353,25 +1412,43 @@ cudaError_t ozaki_prepare_h_tri(int64_t N, const z_t *H, int64_t ldh, OzakiH *oh
 }
 
 cudaError_t ozaki_prepare_bse(int Nk, int Nv, int Nc, const BseModel &md, const double *dE,
-                              const z_t *u, const z_t *a, const double *Kt, OzakiH *oh,
+                              const z_t *u, const z_t *a, const double *Kt, bool tri, OzakiH *oh,
                               ChaseScalars *sc, cudaStream_t st) {
     const int64_t N = (int64_t)Nk * Nv * Nc;
-    const int64_t Np = ozaki_padded(N);
+    const int64_t Np = ozaki_padded(N), Tb = Np / kBM, nslots = Tb * (Tb + 1);
     oh->N = N;
     oh->Np = Np;
-    oh->tri = false;
-    k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
-    bse_count_launches(1);
+    oh->tri = tri;
     const int dyn = 2 * kGT * std::max(md.rank_x, 1) * (int)sizeof(z_t);
-    static std::once_flag once[2][kMaxDevices];
-    static cudaError_t attr[2][kMaxDevices];
+    static std::once_flag once[3][kMaxDevices];
+    static cudaError_t attr[3][kMaxDevices];
     cudaError_t ae = smem_attr_once(once[0], attr[0], (const void *)k_gen_row_exponent, 2 * kGT * 64 * (int)sizeof(z_t));
     if (ae == cudaSuccess)
         ae = smem_attr_once(once[1], attr[1], (const void *)k_gen_slice, 2 * kGT * 64 * (int)sizeof(z_t));
+    if (ae == cudaSuccess)
+        ae = smem_attr_once(once[2], attr[2], (const void *)k_gen_slice_tri, 2 * kGT * 64 * (int)sizeof(z_t));
     if (ae != cudaSuccess) return ae;
     const unsigned T = (unsigned)((N + kGT - 1) / kGT), Tp = (unsigned)(Np / kGT);
+    if (tri) {
+        unsigned long long *Mx = (unsigned long long *)oh->s;
+        ae = cudaMemsetAsync(Mx, 0, (size_t)Np * sizeof(unsigned long long), st);
+        if (ae != cudaSuccess) return ae;
+        k_gen_row_exponent<<<dim3(T, T), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a,
+                                                                  Kt, oh->E, sc, Mx);
+        k_tri_scales<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(N, Np, Mx, oh->t, oh->s, oh->E, sc);
+        k_gen_slice_tri<<<dim3(Tp, Tp), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a,
+                                                                 Kt, oh->s, nslots,
+                                                                 (uint16_t *)oh->A);
+        bse_count_launches(3);
+        if (!make_map((CUtensorMap *)oh->tmap, oh->A, kBM, (uint64_t)(kS * 2 * nslots), kBM) ||
+            !make_map((CUtensorMap *)oh->tmap2, oh->A, kBM, (uint64_t)(kS * 2 * nslots), kBM / 2))
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
+    k_fill_int<<<(unsigned)((Np + 255) / 256), 256, 0, st>>>(oh->E, (int)Np, INT_MIN);
+    bse_count_launches(1);
     k_gen_row_exponent<<<dim3(T, T), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, md, dE, u, a, Kt,
-                                                              oh->E, sc);
+                                                              oh->E, sc, nullptr);
     k_gen_slice<<<dim3(Tp, Tp), dim3(kGT, 8), dyn, st>>>(Nk, Nv * Nc, (int)N, Np, md, dE, u, a, Kt,
                                                         oh->E, (uint16_t *)oh->A);
     bse_count_launches(2);

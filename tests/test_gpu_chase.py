@@ -459,6 +459,11 @@ def test_solve_half_storage(ctx, c1, precision):
     with pytest.raises(pkg.BseError) as ei:
         ctx.solve(Hd, 50, 25, precision=pkg.CHASE_FP64_DFMA, half_storage=True)
     assert ei.value.status == pkg.BSE_EINVAL
+    # the slices generated without H (chase_solve_bse): bit for bit the
+    # half-storage solve of the built H
+    e3, V3, r3, _ = ctx.solve_bse(0, 125, 4, 4, 50, 25, tol=1e-10, deg_max=36,
+                                  precision=precision, half_storage=True)
+    assert np.array_equal(e3, evals) and np.array_equal(r3, resid) and torch.equal(V3, Vd)
 
 
 def test_solve_mixed_precision(ctx, c1):
@@ -519,17 +524,22 @@ def test_solve_nex_tuner_matches_oracle(ctx, c1):
 ])
 def test_solve_bse_without_stored_h_is_bitwise_the_same(ctx, shape, model, precision):
     """chase_solve_bse generates the synthetic Hamiltonian straight into its
-    tensor-core slices; the solve is bit for bit the one on the stored H."""
+    tensor-core slices; the solve is bit for bit the one on the stored H, with
+    full and with half storage of the slices."""
     Nk, Nv, Nc = shape
     N = Nk * Nv * Nc
     nev, nex = min(20, N // 4), min(10, N // 8)
     Hd = ctx.build_hamiltonian(9, Nk, Nv, Nc, model)
     a = ctx.solve(Hd, nev, nex, precision=precision, seed=2)
+    at = ctx.solve(Hd, nev, nex, precision=precision, seed=2, half_storage=True)
     del Hd
     b = ctx.solve_bse(9, Nk, Nv, Nc, nev, nex, precision=precision, model=model, seed_start=2)
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])
-    assert torch.equal(a[1], b[1])
-    assert a[3]["iters"] == b[3]["iters"] and a[3]["matvecs"] == b[3]["matvecs"]
+    bt = ctx.solve_bse(9, Nk, Nv, Nc, nev, nex, precision=precision, model=model, seed_start=2,
+                       half_storage=True)
+    for x, y in ((a, b), (at, bt)):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[2], y[2])
+        assert torch.equal(x[1], y[1])
+        assert x[3]["iters"] == y[3]["iters"] and x[3]["matvecs"] == y[3]["matvecs"]
     with pytest.raises(pkg.BseError) as ei:
         ctx.solve_bse(9, Nk, Nv, Nc, nev, nex, precision=pkg.CHASE_FP64_DFMA)
     assert ei.value.status == pkg.BSE_EINVAL
