@@ -366,16 +366,24 @@ def run_ours(args, rank, world, local_rank):
     W = workload(args)
     N, nev, nex = W["N"], W["nev"], W["nex"]
     ctx = pkg.Context(local_rank)
-    H = pkg.colmajor_empty(N, N, device="cuda:%d" % local_rank)
+    half = args.storage == "half"
+    if args.h_free:
+        args.no_e2e = args.no_extras = args.no_cpu_baseline = True
+    H = None if args.h_free else pkg.colmajor_empty(N, N, device="cuda:%d" % local_rank)
     evecs = pkg.colmajor_empty(N, nev, device="cuda:%d" % local_rank)
     stream = torch.cuda.current_stream()
 
     prec = PRECISIONS[args.precision]
 
     def step():
+        if args.h_free:
+            return ctx.solve_bse(replica_seed(W["seed"], rank), W["Nk"], W["Nv"], W["Nc"], nev,
+                                 nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs,
+                                 precision=prec, degree_group=args.degree_group,
+                                 half_storage=half)
         ctx.build_hamiltonian(replica_seed(W["seed"], rank), W["Nk"], W["Nv"], W["Nc"], out=H)
         return ctx.solve(H, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=evecs,
-                         precision=prec, degree_group=args.degree_group)
+                         precision=prec, degree_group=args.degree_group, half_storage=half)
 
     for _ in range(args.warmup):
         step()
@@ -419,7 +427,8 @@ def run_ours(args, rank, world, local_rank):
         Zh = pkg.host_empty((N, nev))
         t0 = time.perf_counter()
         st_e2e = ctx.solve_host(Hcol, nev, nex, tol=W["tol"], deg_max=W["deg_max"], evecs=Zh,
-                                precision=prec, degree_group=args.degree_group)[3]
+                                precision=prec, degree_group=args.degree_group,
+                                half_storage=half)[3]
         e2e_s = slowest(time.perf_counter() - t0, dist, device="cuda")
         del Hcol, Zh
 
@@ -428,7 +437,7 @@ def run_ours(args, rank, world, local_rank):
     # FP64 solve of the last timed step) and the degrees of Eq. (S1) as they
     # are (no degree groups)
     extras = {}
-    if not args.no_extras and world == 1 and args.precision == "fp64":
+    if not args.no_extras and world == 1 and args.precision == "fp64" and not half:
         ev_ref = stats_evals[-1]
         V_ref = evecs.clone()
 
@@ -510,13 +519,16 @@ def run_ours(args, rank, world, local_rank):
         st = stats[-1]
         sec = ms_max / 1e3 / args.steps
         roof = roofline(args.precision, st, N, W["workload"])
+        if half or args.h_free:
+            roof["traffic"] = None          # the DRAM record is the full-storage kernel's
         line = {
             "metric": METRIC, "value": sec, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision], "data": "synthetic",
             "config": dict(W, precision=args.precision, degree_group=args.degree_group,
-                           parallelism="replicas" if world > 1 else "single"),
+                           parallelism="replicas" if world > 1 else "single",
+                           storage=args.storage, h_stored=not args.h_free),
             "throughput_solves_per_s": replica_throughput(world, args.steps, ms_max),
             "step_ms": {"mean": statistics.mean(step_ms), "min": min(step_ms),
                         "std": statistics.pstdev(step_ms), "n": len(step_ms)},
@@ -684,6 +696,12 @@ def main():
     ap.add_argument("--nk", type=int, default=WORKLOAD["Nk"], help="k-points (N = 16 Nk)")
     ap.add_argument("--nev", type=int, default=WORKLOAD["nev"])
     ap.add_argument("--nex", type=int, default=WORKLOAD["nex"])
+    ap.add_argument("--storage", default="full", choices=["full", "half"],
+                    help="tensor-core slices of all of H (default) or of its lower triangle")
+    ap.add_argument("--h-free", action="store_true",
+                    help="each step solves without storing H (chase_solve_bse: the generator "
+                         "writes the slices); implies --no-e2e, --no-extras and "
+                         "--no-cpu-baseline")
     ap.add_argument("--degree-group", type=int, default=48,
                     help="48 (default): filter degrees raised in groups of one tensor-core "
                          "tile; 0: the per-vector degrees of Eq. (S1) unchanged")
