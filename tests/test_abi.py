@@ -66,3 +66,58 @@ def test_enum_values_match_binding():
     for name, v in vals.items():
         assert getattr(pkg, name) == v, name
     assert vals["CHASE_MIXED_BF16X3"] == 2 and vals["CHASE_FP64_DFMA"] == 3
+
+
+_CTYPES = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+           "double": ctypes.c_double}
+
+
+def header_structs():
+    """Field names and C types of every `typedef struct { ... } name;` of the
+    header, in declaration order (comments removed; `T a, b;` gives two)."""
+    src = open(os.path.join(ROOT, "include", "bsechase.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct \{(.*?)\}\s*(\w+);", src, flags=re.S):
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            mt = re.match(r"((?:const )?[A-Za-z_]\w*(?: \*|\*)*)\s*(.*)", decl)
+            ctype, names = mt.group(1), mt.group(2)
+            for nm in names.split(","):
+                nm = nm.strip()
+                ptr = ctype.endswith("*") or nm.startswith("*")
+                fields.append((nm.lstrip("*").strip(), "ptr" if ptr else ctype.split()[-1]))
+        out[m.group(2)] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("bse_model", "Model"), ("chase_opts", "Opts"),
+                                          ("chase_stats", "Stats"), ("chase_request", "Request"),
+                                          ("chase_result", "Result")])
+def test_struct_layouts_match_binding(cname, pyname):
+    """The ctypes structures of the binding declare the header's fields in the
+    header's order with matching types (appended fields included)."""
+    hdr = header_structs()[cname]
+    py = getattr(pkg, pyname)._fields_
+    assert [n for n, _ in hdr] == [n for n, _ in py]
+    for (n, t), (_, pt) in zip(hdr, py):
+        if t == "ptr":
+            assert pt is ctypes.c_void_p or hasattr(pt, "contents") or pt is ctypes.c_char_p, n
+        elif t in _CTYPES:
+            assert ctypes.sizeof(pt) == ctypes.sizeof(_CTYPES[t]) and pt is _CTYPES[t], n
+        else:                                            # a nested struct
+            assert issubclass(pt, ctypes.Structure), n
+
+
+def test_argument_checks_before_any_device_call(lib):
+    """Entry points added later reject bad arguments without touching a GPU."""
+    p = ctypes.c_void_p()
+    assert lib.bsechase_host_alloc(None, 16) == pkg.BSE_EINVAL
+    assert lib.bsechase_host_alloc(ctypes.byref(p), 0) == pkg.BSE_EINVAL
+    assert lib.bsechase_host_free(None) == pkg.BSE_OK
+    assert lib.chase_hemm_slices(None, None, 1, 1, None, 1, 1, None, 1, 6, 0) == pkg.BSE_EINVAL
+    assert lib.chase_solve_bse(None, 0, 1, 1, 1, None, 1, 0, 1e-10, 36, 0, None, None, None, 1,
+                               None, None) == pkg.BSE_EINVAL
