@@ -684,6 +684,13 @@ def test_solve_full_size_certified(ctx):
     assert np.max(np.abs(ref["evals"] - lam[:nev]) / lam[:nev]) <= 1e-10
     assert np.allclose(evals, ref["evals"], rtol=EVAL_RTOL[pkg.CHASE_FP64], atol=0)
     assert subspace_sin(V, ref["evecs"]) <= 1e-8
+    # half storage of the slices, H not stored: the exact eigenvalues too,
+    # and the same subspace
+    e2, V2, r2, st2 = ctx.solve_bse(0, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36,
+                                    half_storage=True)
+    assert np.max(r2) <= 1e-10
+    assert np.max(np.abs(e2 - lam[:nev]) / np.abs(lam[:nev])) <= 1e-10
+    assert subspace_sin(host(V2), ref["evecs"]) <= 1e-8
 
 
 def test_solve_c3_certified(ctx):
@@ -719,6 +726,12 @@ def test_solve_c3_certified(ctx):
     e3, V3, r3, _ = ctx.solve_bse(0, Nk, 4, 4, nev, nex, tol=1e-10, deg_max=36, degree_group=48)
     assert np.array_equal(e3, evals) and np.array_equal(r3, resid) and torch.equal(V3, Vd)
     del V3
+    # and on half storage without H (30 GB for all of H): the exact eigenvalues
+    e4, V4, r4, _ = ctx.solve_bse(0, Nk, 4, 4, nev, nex, tol=1e-10, deg_max=36, degree_group=48,
+                                  half_storage=True)
+    assert np.max(r4) <= 1e-10
+    assert np.max(np.abs(e4 - lam[:nev]) / np.abs(lam[:nev])) <= 1e-10
+    del V4
     e2, V2, r2, st2 = ctx.solve(Hd, nev, nex, tol=1e-10, deg_max=36, seed=1,
                                 precision=pkg.CHASE_MIXED_FP32, degree_group=48)
     assert np.max(r2) <= 1e-10
