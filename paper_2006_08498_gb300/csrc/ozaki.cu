@@ -1510,7 +1510,7 @@ OzBatch single(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzArgs &a) 
 // queued thread leads: it waits until as many jobs are queued as there are
 // active solvers (each of them is then waiting on a product) or until the
 // window has passed since it began to lead, then launches every queued job
-// of the same precision (up to kMaxJobs, oldest first) on the batcher's
+// of the same kernel configuration (up to kMaxJobs, oldest first) on the batcher's
 // stream behind the jobs' events, records one event after the launch, and
 // hands the lead on.  Every submitter makes its stream wait for that event
 // before its split reduction.  The jobs' units, splits and operands are
@@ -1520,7 +1520,7 @@ struct OzBatcher {
     std::condition_variable cv;
     struct Pending {
         OzJob job;
-        int level = OZ_S6;
+        int cfg = OZ_S6;         // kernel configuration (launch_batch)
         cudaEvent_t ready = nullptr, done = nullptr;
         bool launched = false;
         cudaError_t err = cudaSuccess;
@@ -1590,12 +1590,12 @@ cudaEvent_t ready_event() {
     return ev;
 }
 
-// Run job (with its accuracy level) through the batcher; returns after `st`
-// waits for the launch that contains it.
-cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int level, cudaStream_t st) {
+// Run job (with its kernel configuration) through the batcher; returns after
+// `st` waits for the launch that contains it.
+cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int cfg, cudaStream_t st) {
     OzBatcher::Pending me;
     me.job = job;
-    me.level = level;
+    me.cfg = cfg;
     me.ready = ready_event();
     if (!me.ready) return cudaErrorUnknown;
     cudaError_t e = cudaEventRecord(me.ready, st);
@@ -1617,9 +1617,9 @@ cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int level, cudaStream_t st) 
                b->cv.wait_until(lk, t_end) != std::cv_status::timeout) {
         }
         std::vector<OzBatcher::Pending *> take;
-        const int level0 = b->queue.front()->level;
+        const int cfg0 = b->queue.front()->cfg;
         for (auto it = b->queue.begin(); it != b->queue.end() && (int)take.size() < kMaxJobs;) {
-            if ((*it)->level == level0) {
+            if ((*it)->cfg == cfg0) {
                 take.push_back(*it);
                 it = b->queue.erase(it);
             } else {
@@ -1649,7 +1649,7 @@ cudaError_t ozb_run(OzBatcher *b, const OzJob &job, int level, cudaStream_t st) 
         }
         for (size_t k = 0; k < take.size() && le == cudaSuccess; k++)
             le = cudaStreamWaitEvent(b->st, take[k]->ready, 0);
-        if (le == cudaSuccess) le = launch_batch(bt, level0, b->sms, b->st);
+        if (le == cudaSuccess) le = launch_batch(bt, cfg0, b->sms, b->st);
         if (le == cudaSuccess) le = cudaEventRecord(done, b->st);
         lk.lock();
         for (auto *p : take) {
