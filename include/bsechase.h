@@ -134,8 +134,12 @@ typedef struct {
                             H = T S T with t_i = sqrt(max_k |H_ik|), so that
                             one exponent serves S's rows and its columns, and
                             the product reads each stored tile of S both
-                            ways.  Tensor-core precisions only (BSE_EINVAL
-                            otherwise).  With chase_solve_bse the slices are
+                            ways.  The products keep the normwise accuracy
+                            of full storage; row by row it is relative to
+                            sqrt(max_k |H_ik| max |H|) rather than to the
+                            row's own maximum, so the small rows of a
+                            strongly graded H are less accurate.  Tensor-core
+                            precisions only (BSE_EINVAL otherwise).  With chase_solve_bse the slices are
                             generated, so H's whole footprint is 12 N^2
                             bytes. */
 } chase_opts;
