@@ -689,7 +689,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--serving", action="store_true", help="run the serving mix instead")
     ap.add_argument("--requests", type=int, default=256)
-    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=3,
+                    help="serving: concurrent solves (3: the p99 minimum at full throughput)")
     ap.add_argument("--batch-window", type=float, default=None,
                     help="serving: run concurrent solves' products in shared launches, "
                          "waiting up to this many seconds for company (default: off)")
