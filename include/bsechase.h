@@ -360,6 +360,11 @@ typedef struct {
                                 read by the solve and not copied: the caller
                                 keeps it unchanged until the request finishes */
     int64_t ldh;
+    int half_storage;        /* as chase_opts.half_storage                     */
+    int h_free;              /* 1: the synthetic Hamiltonian is not stored (as
+                                chase_solve_bse; tensor-core precisions, d_H
+                                NULL): 16 N^2 bytes less in the request's
+                                budget estimate                               */
 } chase_request;
 
 typedef struct {

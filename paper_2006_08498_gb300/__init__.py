@@ -82,7 +82,7 @@ class Request(ctypes.Structure):
                 ("deg_max", ctypes.c_int), ("precision", ctypes.c_int),
                 ("warm_ticket", ctypes.c_uint64), ("degree_group", ctypes.c_int),
                 ("nex_damping", ctypes.c_double), ("d_H", ctypes.c_void_p),
-                ("ldh", ctypes.c_int64)]
+                ("ldh", ctypes.c_int64), ("half_storage", ctypes.c_int), ("h_free", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -474,11 +474,13 @@ class Context:
         self._check(load().chase_server_destroy(self._h))
 
     def submit(self, seed, Nk, Nv, Nc, nev, nex, tol=1e-10, deg_max=36, precision=CHASE_FP64,
-               model=None, warm_ticket=0, degree_group=0, nex_damping=0.0, H=None):
+               model=None, warm_ticket=0, degree_group=0, nex_damping=0.0, H=None,
+               half_storage=False, h_free=False):
         """Queue a solve of the synthetic Hamiltonian (seed, Nk, Nv, Nc), or of
         the caller's device matrix H (N = Nk Nv Nc, column-major; kept alive
         and unchanged by the caller until the request finishes); returns its
-        ticket."""
+        ticket.  half_storage: slices of H's lower triangle only; h_free: the
+        synthetic H is not stored (chase_solve_bse)."""
         md = dict(DEFAULT_MODEL)
         if model:
             md.update(model)
@@ -487,7 +489,7 @@ class Context:
                           int(md["rank_x"])),
                     nev, nex, tol, deg_max, precision, warm_ticket, degree_group, nex_damping,
                     None if H is None else ctypes.c_void_p(H.data_ptr()),
-                    0 if H is None else _ld(H))
+                    0 if H is None else _ld(H), int(half_storage), int(h_free))
         t = ctypes.c_uint64(0)
         self._check(load().chase_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value

@@ -258,11 +258,11 @@ int hop_apply(bsechase_ctx *ctx, const Hop &op, int n, const z_t *Y, int64_t ldy
     return BSE_OK;
 }
 
+}  // namespace
+
 bool precision_uses_tc(int precision) {
     return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32;
 }
-
-}  // namespace
 
 bool precision_valid(int precision) {
     return precision == CHASE_FP64 || precision == CHASE_MIXED_FP32 ||
@@ -752,9 +752,7 @@ struct DeviceGuard {
 
 }  // namespace
 
-namespace {
-
-BseModel model_of(const bse_model *model) {
+BseModel bse_model_of(const bse_model *model) {
     BseModel md{2.0, 0.3, 0.5, 0.01, 1.0, 8};
     if (model) {
         md.band_gap = model->band_gap;
@@ -766,6 +764,8 @@ BseModel model_of(const bse_model *model) {
     }
     return md;
 }
+
+namespace {
 
 // The generator's tables in the context's workspace: u[N] and a[N R] first
 // (16-byte aligned), then dE[N] and Kt[Nk/2 + 1].
@@ -783,6 +783,15 @@ int bse_tables(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc, const B
 }
 
 }  // namespace
+
+int bse_source(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+               BseSource *src) {
+    int rc;
+    if ((rc = bse_tables(ctx, seed, Nk, Nv, Nc, md, src))) return rc;
+    CK(launch_bse_tables(seed, Nk, Nv, Nc, md, (double *)src->dE, (z_t *)src->u, (z_t *)src->a,
+                         (double *)src->Kt, ctx->st));
+    return BSE_OK;
+}
 
 // =================================================================== ABI
 
@@ -891,7 +900,7 @@ int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int 
     if (!ctx) return BSE_EINVAL;
     const int64_t N = bse_dim(Nk, Nv, Nc);
     if (N < 1 || !d_H || ldh < N) return fail(ctx, BSE_EINVAL, "bad sizes or NULL H%s");
-    const BseModel md = model_of(model);
+    const BseModel md = bse_model_of(model);
     if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
     DeviceGuard g(ctx->device);
     int rc;
@@ -910,7 +919,7 @@ int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
     if (!ctx) return BSE_EINVAL;
     const int64_t N = bse_dim(Nk, Nv, Nc);
     if (N < 1) return fail(ctx, BSE_EINVAL, "bad sizes%s");
-    const BseModel md = model_of(model);
+    const BseModel md = bse_model_of(model);
     if (md.rank_x < 0 || md.rank_x > 64) return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
     if (!h_evals || !d_evecs || !h_resid) return fail(ctx, BSE_EINVAL, "NULL output%s");
     // the checks of chase_solve, with the (absent) matrix's place taken by an output
@@ -921,9 +930,7 @@ int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
     DeviceGuard g(ctx->device);
     ctx->err.clear();
     BseSource src;
-    if ((rc = bse_tables(ctx, seed, Nk, Nv, Nc, md, &src))) return rc;
-    CK(launch_bse_tables(seed, Nk, Nv, Nc, md, (double *)src.dE, (z_t *)src.u, (z_t *)src.a,
-                         (double *)src.Kt, ctx->st));
+    if ((rc = bse_source(ctx, seed, Nk, Nv, Nc, md, &src))) return rc;
     return solve_device(ctx, nullptr, N, N, nev, nex, tol, deg_max, precision_mode(precision),
                         opts, h_evals, (z_t *)d_evecs, ldz, h_resid, stats, &src);
 }

@@ -63,6 +63,12 @@ struct BseSource {
     const double *dE, *Kt;
     const z_t *u, *a;
 };
+// The model parameters of a bse_model (NULL: the defaults), and the
+// generator's tables of (seed, Nk, Nv, Nc, md) written into the context's
+// workspace as the source of a solve without the stored H.
+BseModel bse_model_of(const bse_model *model);
+int bse_source(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc, const BseModel &md,
+               BseSource *src);
 // The whole solve on device buffers (chase_solve without argument checks);
 // with `bse` set, H is that source's and `H` is unused.
 int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int nev, int nex,
@@ -73,6 +79,8 @@ int solve_device(bsechase_ctx *ctx, const z_t *H, int64_t N, int64_t ldh, int ne
 // (CHASE_MIXED_BF16X3 runs as CHASE_MIXED_FP32).
 bool precision_valid(int precision);
 int precision_mode(int precision);
+// Whether a (mode) precision computes the products with H on the tensor cores.
+bool precision_uses_tc(int precision);
 // Add the recorded tensor-core launch times to k_ms / k_flops / k_launches
 // (the stream must have been synchronised) and recycle the events.
 void harvest_kernel_times(bsechase_ctx *ctx);

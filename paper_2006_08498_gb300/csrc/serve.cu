@@ -80,7 +80,7 @@ struct BseServer {
 
 namespace {
 
-size_t estimate_run_bytes(int64_t N, int m, int nev, int precision, bool own_h) {
+size_t estimate_run_bytes(int64_t N, int m, int nev, int precision, bool own_h, bool half) {
     const size_t Np = (size_t)ozaki_padded(N);
     const size_t mp = (size_t)((std::max(m, 32) + 31) / 32 * 32);
     size_t b = own_h ? 16 * (size_t)N * N : 0;              // H, unless the caller's
@@ -88,7 +88,8 @@ size_t estimate_run_bytes(int64_t N, int m, int nev, int precision, bool own_h) 
     b += 16 * (size_t)N * nev;                              // eigenvectors
     b += (size_t)N * 8 * 3 * 16 + ((size_t)20 << 20);       // Lanczos blocks, small matrices
     if (precision != CHASE_FP64_DFMA) {
-        b += 24 * Np * Np;                                  // slices of H
+        b += half ? ozaki_a_bytes_tri(N) + 16 * Np          // slices of H (half storage:
+                  : 24 * Np * Np;                           // the lower triangle, scales)
         b += 36 * mp * Np;                                  // slices of the operand
         b += ozaki_partial_bytes(N, std::max(m, 32));       // split-K partials
         b += std::max(ozaki_gen_a_bytes(std::max(m, 32), N),  // slices of op(A) in the
@@ -165,20 +166,27 @@ void worker(BseServer *S, int slot) {
         const int64_t N = job->N;
         void *dH = nullptr, *dZ = nullptr;
         int rc = BSE_OK;
-        if ((!rq.d_H && cudaMallocAsync(&dH, 16 * (size_t)N * N, ctx->st) != cudaSuccess) ||
+        const bool store_h = !rq.d_H && !rq.h_free;
+        if ((store_h && cudaMallocAsync(&dH, 16 * (size_t)N * N, ctx->st) != cudaSuccess) ||
             cudaMallocAsync(&dZ, 16 * (size_t)N * rq.nev, ctx->st) != cudaSuccess) {
             cudaGetLastError();
             rc = BSE_ENOMEM;
         }
-        if (rc == BSE_OK && !rq.d_H)
+        if (rc == BSE_OK && store_h)
             rc = bse_build_hamiltonian(ctx, rq.seed, rq.Nk, rq.Nv, rq.Nc,
                                        rq.use_model ? &rq.model : nullptr, dH, N);
+        // h_free: the generator's tables, its elements go straight into the slices
+        BseSource src{};
+        if (rc == BSE_OK && rq.h_free)
+            rc = bse_source(ctx, rq.seed, rq.Nk, rq.Nv, rq.Nc,
+                            bse_model_of(rq.use_model ? &rq.model : nullptr), &src);
         const z_t *Hs = rq.d_H ? (const z_t *)rq.d_H : (const z_t *)dH;
         const int64_t lds = rq.d_H ? rq.ldh : N;
         chase_opts o{};
         o.seed = rq.seed;
         o.degree_group = rq.degree_group;
         o.nex_damping = rq.nex_damping;
+        o.half_storage = rq.half_storage;
         if (warm) {
             o.d_V0 = warm->d_evecs;
             o.ldv0 = N;
@@ -187,8 +195,9 @@ void worker(BseServer *S, int slot) {
         std::vector<double> ev(rq.nev), rs(rq.nev);
         chase_stats st{};
         if (rc == BSE_OK)
-            rc = solve_device(ctx, Hs, N, lds, rq.nev, rq.nex, rq.tol, rq.deg_max,
-                              rq.precision, &o, ev.data(), (z_t *)dZ, N, rs.data(), &st);
+            rc = solve_device(ctx, rq.h_free ? nullptr : Hs, N, rq.h_free ? N : lds, rq.nev,
+                              rq.nex, rq.tol, rq.deg_max, rq.precision, &o, ev.data(), (z_t *)dZ,
+                              N, rs.data(), &st, rq.h_free ? &src : nullptr);
         if (dH) cudaFreeAsync(dH, ctx->st);
         release_workspace(ctx);
         cudaStreamSynchronize(ctx->st);
@@ -288,14 +297,21 @@ int chase_server_submit(bsechase_ctx *ctx, const chase_request *req, uint64_t *t
     const int64_t N = bse_dim(req->Nk, req->Nv, req->Nc);
     const int m = req->nev + req->nex;
     if (N < 1 || req->nev < 1 || req->nex < 0 || m > N || m > 512 || !(req->tol > 0) ||
-        req->deg_max < 2 || req->degree_group < 0 || !precision_valid(req->precision))
+        req->deg_max < 2 || req->degree_group < 0 || !precision_valid(req->precision) ||
+        (req->half_storage != 0 && req->half_storage != 1) || (req->h_free != 0 && req->h_free != 1))
         return fail(ctx, BSE_EINVAL, "invalid request%s");
+    if ((req->half_storage || req->h_free) && !precision_uses_tc(precision_mode(req->precision)))
+        return fail(ctx, BSE_EINVAL, "half_storage and h_free need a tensor-core precision%s");
+    if (req->h_free && req->d_H) return fail(ctx, BSE_EINVAL, "h_free with a caller's H%s");
+    if (req->use_model && (req->model.rank_x < 0 || req->model.rank_x > 64))
+        return fail(ctx, BSE_EINVAL, "rank_x outside 0..64%s");
     auto q = std::make_shared<Req>();
     q->rq = *req;
     q->rq.precision = precision_mode(req->precision);
     q->N = N;
     if (req->d_H && req->ldh < N) return fail(ctx, BSE_EINVAL, "request H: ldh < N%s");
-    q->run_bytes = estimate_run_bytes(N, m, req->nev, q->rq.precision, req->d_H == nullptr);
+    q->run_bytes = estimate_run_bytes(N, m, req->nev, q->rq.precision,
+                                      req->d_H == nullptr && !req->h_free, req->half_storage == 1);
     if (q->run_bytes > S->budget)
         return fail(ctx, BSE_ENOMEM, "request needs more than the whole HBM budget%s");
     q->t_submit = now_s();

@@ -84,6 +84,44 @@ def test_server_result_equals_direct_solve(ctx):
     ctx.server_destroy()
 
 
+def test_server_storage_options_equal_direct_solves(ctx):
+    """Requests without the stored H (h_free) and on half storage: bit for
+    bit the direct solves of the same kind (chase_solve_bse, chase_opts.
+    half_storage); a smaller budget estimate admits the H-free request where
+    the stored one is refused; invalid combinations are rejected."""
+    Hd = ctx.build_hamiltonian(3, 63, 4, 4)
+    eh, Vh, _, _ = ctx.solve(Hd, 20, 10, seed=3, half_storage=True)
+    ef, Vf, _, _ = ctx.solve_bse(3, 63, 4, 4, 20, 10, seed_start=3)
+    eb, Vb, _, _ = ctx.solve_bse(3, 63, 4, 4, 20, 10, seed_start=3, half_storage=True)
+    N = Hd.shape[0]
+    del Hd
+    ctx.server_create(16 * GB, 3)
+    tickets = [ctx.submit(seed=3, Nk=63, Nv=4, Nc=4, nev=20, nex=10, half_storage=True),
+               ctx.submit(seed=3, Nk=63, Nv=4, Nc=4, nev=20, nex=10, h_free=True),
+               ctx.submit(seed=3, Nk=63, Nv=4, Nc=4, nev=20, nex=10, h_free=True,
+                          half_storage=True)]
+    for t, (e, V) in zip(tickets, ((eh, Vh), (ef, Vf), (eb, Vb))):
+        res = ctx.wait(t)
+        assert res["status"] == pkg.BSE_OK
+        assert np.array_equal(res["evals"], e)
+        assert torch.equal(ctx.fetch_evecs(t, N, 20), V)
+    for bad in (dict(h_free=True, precision=pkg.CHASE_FP64_DFMA),
+                dict(half_storage=True, precision=pkg.CHASE_FP64_DFMA),
+                dict(h_free=True, H=pkg.colmajor_empty(N, N).zero_())):
+        with pytest.raises(pkg.BseError) as ei:
+            ctx.submit(seed=3, Nk=63, Nv=4, Nc=4, nev=20, nex=10, **bad)
+        assert ei.value.status == pkg.BSE_EINVAL
+    ctx.server_destroy()
+    # N = 8000: the stored H alone is 1 GB; a budget between the two estimates
+    ctx.server_create(int(2.0 * GB), 1)
+    with pytest.raises(pkg.BseError) as ei:
+        ctx.submit(seed=1, Nk=500, Nv=4, Nc=4, nev=20, nex=10)
+    assert ei.value.status == pkg.BSE_ENOMEM
+    t = ctx.submit(seed=1, Nk=500, Nv=4, Nc=4, nev=20, nex=10, h_free=True, half_storage=True)
+    assert ctx.wait(t)["status"] == pkg.BSE_OK
+    ctx.server_destroy()
+
+
 def test_admission_by_budget(ctx):
     # one N = 2000 request is estimated at ~0.19 GB (H 64 MB, slices of H
     # 100 MB, search space and workspace): a 0.3 GB budget admits one at a time
