@@ -34,6 +34,7 @@
 #ifndef BSECHASE_H
 #define BSECHASE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -226,7 +227,8 @@ int bse_build_hamiltonian(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int 
  * Outputs: h_evals[nev] ascending; d_evecs (N x nev complex128, ld = ldz >=
  * N) orthonormal, each column's largest-modulus entry (smallest index on
  * ties) real and positive; h_resid[nev]; stats (nullable).
- * d_H is read only.  Errors: BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV (outputs
+ * d_H is read only (with chase_opts.half_storage, only its lower triangle).
+ * Errors: BSE_EINVAL, BSE_ENOMEM, BSE_ENOCONV (outputs
  * filled, unconverged residuals +inf), BSE_ENONFINITE, BSE_ECUDA. */
 int chase_solve(bsechase_ctx *ctx, const void *d_H, int64_t N, int64_t ldh, int nev, int nex,
                 double tol, int deg_max, int precision, const chase_opts *opts, double *h_evals,
@@ -253,8 +255,10 @@ int chase_solve_bse(bsechase_ctx *ctx, uint64_t seed, int Nk, int Nv, int Nc,
  * upper triangle is taken as its conjugate transpose (H is Hermitian; the
  * paper's reader likewise holds one triangle, Sec. 3), and the eigenvectors
  * are copied back into h_evecs (N x nev, ld = ldz).  The strict upper triangle
- * of h_H is never read.  Host buffers should be pinned for full transfer
- * speed.  Same errors as chase_solve. */
+ * of h_H is never read.  Host buffers should be page-locked
+ * (bsechase_host_alloc) for full transfer speed; stats, when given, also
+ * report the bytes copied each way and the copy's time.  Same errors as
+ * chase_solve. */
 int chase_solve_host(bsechase_ctx *ctx, const void *h_H, int64_t N, int64_t ldh, int nev,
                      int nex, double tol, int deg_max, int precision, const chase_opts *opts,
                      double *h_evals, void *h_evecs, int64_t ldz, double *h_resid,
