@@ -121,3 +121,20 @@ def test_argument_checks_before_any_device_call(lib):
     assert lib.chase_hemm_slices(None, None, 1, 1, None, 1, 1, None, 1, 6, 0) == pkg.BSE_EINVAL
     assert lib.chase_solve_bse(None, 0, 1, 1, 1, None, 1, 0, 1e-10, 36, 0, None, None, None, 1,
                                None, None) == pkg.BSE_EINVAL
+
+
+def test_header_compiles_as_c99(tmp_path):
+    """The boundary is a C ABI: the header compiles as plain C99, warnings
+    as errors."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "bsechase.h"\nint main(void) { chase_stats s; chase_opts o; '
+                   'chase_request r; (void)s; (void)o; (void)r; return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                        str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
